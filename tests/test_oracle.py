@@ -1,0 +1,263 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+closed forms (Fibonacci numbers, exact rewrite and sweep counts derived by
+hand from the rules), values printed in the paper (tests/golden), strategy
+independence, and brute-force exploration of every reduction sequence."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import trs_inputs as ti
+from oracle import Oracle, OracleError, brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_examples.txt")
+TRS_BY_NAME = {t.name: t for t in (ti.FIB, ti.ARITH, ti.MSORT, ti.TTREE, ti.PAPER_FFA,
+                                   ti.PAPER_PLUS, ti.NONTERM)}
+
+
+def parse(trs, text):
+    toks = re.findall(r"[A-Za-z0-9_]+|[(),]", text)
+    pos = 0
+    out = []
+
+    def rec():
+        nonlocal pos
+        name = toks[pos]; pos += 1
+        out.append(trs.id[name])
+        if pos < len(toks) and toks[pos] == "(":
+            pos += 1
+            while True:
+                rec()
+                if toks[pos] == ",":
+                    pos += 1
+                    continue
+                assert toks[pos] == ")"
+                pos += 1
+                break
+
+    rec()
+    return np.array(out, dtype=np.int32)
+
+
+def fib_numbers(n):
+    a, b = 0, 1
+    out = []
+    for _ in range(n + 1):
+        out.append(a)
+        a, b = b, a + b
+    return out
+
+
+def fib_rewrites(n):
+    """T(0)=T(1)=1; fib(S(S(x))) costs one step, both recursive calls, and the
+    final plus(S^F(n-2)(0), y), which peels F(n-2) successors and then applies
+    plus(0,y) -> y: T(n) = T(n-1) + T(n-2) + F(n-2) + 2."""
+    F = fib_numbers(n)
+    T = [1, 1]
+    for k in range(2, n + 1):
+        T.append(T[k - 1] + T[k - 2] + F[k - 2] + 2)
+    return T[n]
+
+
+def value(trs, pre):
+    """Value v of a numeral S^v(0) given in preorder."""
+    succ = trs.id.get("S", trs.id.get("Suc"))
+    assert all(x == succ for x in pre[:-1])
+    return len(pre) - 1
+
+
+# --------------------------------------------------------------------------
+# golden values from the paper
+
+
+def golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        rows.append([c.strip() for c in line.split("|")])
+    return rows
+
+
+@pytest.mark.parametrize("row", [r for r in golden_rows() if r[2] in ("innermost", "any")],
+                         ids=lambda r: f"{r[0]}:{r[1]}:{r[2]}")
+def test_paper_worked_examples(row):
+    trs = TRS_BY_NAME[row[0]]
+    term = parse(trs, row[1])
+    if row[2] == "innermost":
+        res = Oracle(trs).normalize(term)
+        assert trs.show(res.term) == row[3]
+    else:
+        expect = {tuple(parse(trs, x.strip())) for x in row[3].split(";")}
+        assert brute.normal_forms(trs, term) == expect
+
+
+def test_paper_ffa_outermost_differs():
+    """Sec. 2: the outermost reduction of f(f(f(a))) yields a, innermost f(a)."""
+    trs = ti.PAPER_FFA
+    o = Oracle(trs)
+    t = parse(trs, "f(f(f(a)))")
+    assert trs.show(o.normalize(t, "outermost").term) == "a"
+    assert trs.show(o.normalize(t, "parallel").term) == "f(a)"
+
+
+def test_plus_s_zero_one_step():
+    """Sec. 3: Plus(S(0), X) -> S(X) is one rewrite."""
+    trs = ti.PAPER_PLUS
+    r = Oracle(trs).normalize(parse(trs, "Plus(S(Zero),S(S(Zero)))"))
+    assert trs.show(r.term) == "S(S(S(Zero)))" and r.rewrites == 1
+
+
+def test_nonterminating_hits_step_cap():
+    """Sec. 2: f(a) -> f(f(a)) has an infinite reduction."""
+    trs = ti.NONTERM
+    o = Oracle(trs)
+    for mode in ("innermost", "parallel", "outermost"):
+        with pytest.raises(OracleError) as e:
+            o.normalize(parse(trs, "f(a)"), mode, step_cap=500)
+        assert e.value.status == 2
+
+
+def test_transformation_tree_leaf_rewrites():
+    """Sec. 4: each of the 2^N leaves is rewritten 26 times; with the 2^(N+1)-1
+    Expand/Expand2 steps the total is 28*2^N - 1; the result is a complete Node
+    tree with End leaves."""
+    o = Oracle(ti.TTREE)
+    for n in range(0, 9):
+        r = o.normalize(ti.ttree_term(n))
+        assert r.rewrites == 28 * 2 ** n - 1
+        assert r.rule_counts[4:].sum() == 26 * 2 ** n
+        assert len(r.term) == 2 ** (n + 1) - 1
+        leaves = [x for x in r.term if x != ti.TTREE.id["Node"]]
+        assert leaves == [ti.TTREE.id["End"]] * 2 ** n
+
+
+# --------------------------------------------------------------------------
+# closed forms
+
+
+@pytest.mark.parametrize("mode", ["innermost", "parallel"])
+def test_fib_closed_form(mode):
+    o = Oracle(ti.FIB)
+    F = fib_numbers(18)
+    for n in range(0, 19 if mode == "innermost" else 14):
+        r = o.normalize(ti.fib_term(n), mode)
+        assert value(ti.FIB, r.term) == F[n]
+        assert r.rewrites == fib_rewrites(n)
+
+
+def test_fib_paper_sizes():
+    """fib(15) = 610 after 5,244 rewrites; fib(22) = 17,711 after 186,579."""
+    o = Oracle(ti.FIB)
+    r = o.normalize(ti.fib_term(15))
+    assert value(ti.FIB, r.term) == 610 and r.rewrites == 5244
+    r = o.normalize(ti.fib_term(22))
+    assert value(ti.FIB, r.term) == 17711 and r.rewrites == 186579
+
+
+def test_parallel_sweeps_plus_closed_form():
+    """Sweeps of plus(S^a(0), S^b(0)) under synchronous parallel innermost:
+    the two numerals become normal forms bottom-up, one level per sweep
+    (max(a,b)+1 sweeps), plus fires in the next sweep and peels one S per sweep
+    (a sweeps), plus(0,y) -> y fires once more, then the a new S nodes above it
+    are marked normal form one per sweep: max(a,b) + 2 + 2a."""
+    o = Oracle(ti.FIB)
+    P = ti.FIB
+    for a in range(0, 9):
+        for b in range(0, 9):
+            t = np.concatenate([[P.id["plus"]], ti.peano(P, a), ti.peano(P, b)])
+            r = o.normalize(t, "parallel")
+            assert r.sweeps == max(a, b) + 2 + 2 * a, (a, b)
+            assert value(P, r.term) == a + b and r.rewrites == a + 1
+
+
+def test_parallel_sweeps_ttree_closed_form():
+    """Expand(Suc^N(Zero)): N+1 sweeps make the numeral normal, N sweeps expand
+    one level each, one sweep turns every Expand(Zero) into A, 26 sweeps walk
+    A..Z -> End, one marks End, N mark the Node levels: 3N + 29."""
+    o = Oracle(ti.TTREE)
+    for n in range(0, 8):
+        assert o.normalize(ti.ttree_term(n), "parallel").sweeps == 3 * n + 29
+
+
+def _arith_expect(meta):
+    depth, ops, vals = meta
+    nl = 1 << depth
+    cost = 0
+    for h in range(1, nl):
+        a, b = int(vals[2 * h]), int(vals[2 * h + 1])
+        # plus(S^a,y): a peels + plus(0,y)->y.  times(S^a,S^b): a+1 times steps
+        # and a plus(S^b, .) calls of b+1 steps each.
+        cost += a * (b + 2) + 1 if ops[h] else a + 1
+        # value at h is checked independently below
+        assert vals[h] == (a * b if ops[h] else a + b)
+    return int(vals[1]), cost
+
+
+@pytest.mark.parametrize("mode", ["innermost", "parallel", "outermost"])
+def test_arith_trees_closed_form(mode):
+    flat, offs, meta = ti.arith_batch(seed=3, count=12, dmin=1, dmax=5)
+    o = Oracle(ti.ARITH)
+    for t, m in zip(ti.split_terms(flat, offs), meta):
+        v, cost = _arith_expect(m)
+        r = o.normalize(t, mode)
+        assert value(ti.ARITH, r.term) == v
+        if mode != "outermost":
+            assert r.rewrites == cost
+
+
+@pytest.mark.parametrize("mode", ["innermost", "parallel"])
+def test_merge_sort_sorts(mode):
+    term, lists = ti.msort_batch(seed=5, nlists=4, lmin=0, lmax=9, vmax=6)
+    r = Oracle(ti.MSORT).normalize(term, mode)
+    expect = ti.msort_tree([sorted(l) for l in lists])
+    # the Sort symbols are gone: Leaf(list) where the input had Leaf(Sort(list))
+    expect = expect[expect != ti.MSORT.id["Sort"]]
+    assert np.array_equal(r.term, expect)
+
+
+def test_strategy_independence():
+    """Innermost, outermost and synchronous-parallel normal forms agree on the
+    confluent workloads (counts are strategy-dependent only for outermost)."""
+    cases = [(ti.FIB, ti.fib_term(n)) for n in range(0, 11)]
+    cases += [(ti.TTREE, ti.ttree_term(n)) for n in range(0, 5)]
+    term, _ = ti.msort_batch(seed=9, nlists=2, lmin=1, lmax=7, vmax=5)
+    cases.append((ti.MSORT, term))
+    for trs, t in cases:
+        o = Oracle(trs)
+        ri, ro, rp = (o.normalize(t, m) for m in ("innermost", "outermost", "parallel"))
+        assert np.array_equal(ri.term, ro.term) and np.array_equal(ri.term, rp.term)
+        assert ri.rewrites == rp.rewrites and ri.nf_marks == rp.nf_marks
+
+
+# --------------------------------------------------------------------------
+# brute force
+
+
+@pytest.mark.parametrize("trs,size", [(ti.FIB, 7), (ti.ARITH, 8), (ti.MSORT, 4),
+                                      (ti.PAPER_PLUS, 6)])
+def test_brute_force_unique_normal_form(trs, size):
+    o = Oracle(trs)
+    terms = brute.ground_terms(trs, size)
+    assert len(terms) > 20
+    for t in terms:
+        nfs = brute.normal_forms(trs, t)
+        assert len(nfs) == 1, trs.show(t)
+        for mode in ("innermost", "parallel"):
+            r = o.normalize(np.array(t, dtype=np.int32), mode)
+            assert tuple(r.term) == next(iter(nfs)), trs.show(t)
+
+
+def test_planted_mistakes_are_caught():
+    """A plausible slip in the rules (a swapped argument, a dropped S) changes
+    what the pins above see; guards that the pins are sensitive."""
+    bad = ti.TRS("fib-bad", [("0", 0), ("S", 1), ("plus", 2), ("fib", 1)],
+                 [(("plus", "0", ti.Y), ti.Y),
+                  (("plus", ("S", ti.X), ti.Y), ("S", ("plus", ti.X, ti.Y))),
+                  (("fib", "0"), "0"),
+                  (("fib", ("S", "0")), ("S", "0")),
+                  (("fib", ("S", ("S", ti.X))), ("plus", ("fib", ti.X), ("fib", ti.X)))])
+    r = Oracle(bad).normalize(ti.fib_term(10))
+    assert value(ti.FIB, r.term) != fib_numbers(10)[10]
