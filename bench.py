@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the term-rewriting engine: node-rewrites/s on Peano fib(22).
+
+Workload: one term fib(S^22(0)) in a node pool of 2^24 slots, normalised to
+S^17711(0) (186,579 rewrites).  A step is one normalisation of that term
+through the C ABI; the term is uploaded before each step's timed region
+(inputs resident in HBM), and L2 is flushed between steps.  The headline
+engine runs next to the plain all-node sweep (the paper's topology-driven
+derive kernel) on the same term.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 (torchrun, one rank per GPU) every rank normalises its own replica
+of the term (a single term does not shard: replicas only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import trs_inputs as ti  # noqa: E402
+
+METRIC = "node-rewrites/sec and time-to-normal-form vs plain sweep; % HBM roofline"
+UNIT = "node-rewrites/s"
+WORKLOAD = "peano fib(22) single term, node pool 2^24 int32 slots"
+POOL = 1 << 24
+FIB_N = 22
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, local
+
+
+def reduce_max(x):
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        return x
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_initialized():
+        dist.barrier()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            out, _ = self.p.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def alg_bytes(st, trace, ma):
+    """Algorithmic bytes of one normalisation (the byte model of the design
+    notes): the all-slot stamp scans, the per-node reads of visited nodes and
+    their arguments' stamps, the writes of rewrites and new nodes, and the
+    garbage-collection and seed scans."""
+    node = 4 + 4 * ma                     # head + argument indices
+    b = 0
+    if trace:
+        b += sum(r[5] for r in trace) * 4 if st["mode"] == "plain" else 0
+    b += st["visits"] * (node + 4 * ma + 4)          # node, argument stamps, own stamp
+    b += st["rewrites"] * (node + 2 * 8 + 3 * 4)     # write node, ~2 pattern gathers, ~3 count atomics
+    b += st["allocs"] * (node + 16)                  # new node: head, args, count, stamp, parent, pending
+    b += st["nf_marks"] * 8                          # stamp write, parent's pending count
+    b += st["gc_runs"] * st["high_water"] * 8 + st["frees"] * (node + 4)
+    b += (st["confirm_sweeps"] + (1 if st["mode"] != "plain" else 0)) * st["high_water"] * 4
+    if st["mode"] != "plain":
+        b += st["visits"] * 8                        # frontier entry read + push
+    return b
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    import paper_2009_07174_gb300 as trs
+    from paper_2009_07174_gb300 import autotune_defaults
+
+    torch.cuda.set_device(local)
+    term = ti.fib_term(FIB_N)
+    prog = trs.trs_compile(ti.FIB)
+    pool = trs.Pool(prog, POOL)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    opts_kw = autotune_defaults(args.mode)
+    mode = opts_kw["mode"]
+    stream = torch.cuda.current_stream()
+
+    def one(opts_kw, trace=0):
+        pool.trs_pool_reset()
+        root = pool.term_upload(term)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pool.trs_normalize(wait=False, trace=trace, **opts_kw)
+        e1.record(stream)
+        return root, e0, e1
+
+    # warm-up (also checks the result once)
+    for _ in range(max(args.warmup, 3)):
+        root, e0, e1 = one(opts_kw)
+    st = pool.trs_pool_stats()
+    res = pool.term_download(root)
+    assert len(res) == 17712 and st["rewrites"] == 186579, st
+
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            root, e0, e1 = one(opts_kw)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(times) / len(times)
+    ms_max = reduce_max(ms)
+    st = pool.trs_pool_stats()
+    rewrites = st["rewrites"]
+    value = rewrites * ws / (ms_max / 1e3)
+
+    # roofline of the engine kernel (one launch per step) with the per-sweep trace
+    root, e0, e1 = one(opts_kw, trace=1)
+    torch.cuda.synchronize()
+    tr = pool.trs_trace_read()
+    st_tr = pool.trs_pool_stats()
+    st_tr["mode"] = mode
+    nbytes = alg_bytes(st_tr, tr, prog.maxarity)
+    peak, peak_kind = peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+
+    # plain all-node sweep on the same term (the method without the frontier)
+    plain_kw = dict(opts_kw, mode="plain")
+    root, e0, e1 = one(plain_kw)
+    torch.cuda.synchronize()
+    plain_times = []
+    for _ in range(2):
+        root, e0, e1 = one(plain_kw)
+        e1.synchronize()
+        plain_times.append(e0.elapsed_time(e1))
+    plain_ms = sum(plain_times) / len(plain_times)
+    plain_st = pool.trs_pool_stats()
+    assert plain_st["rewrites"] == 186579
+
+    # end to end through the C ABI with host buffers: upload, normalise, download
+    e2e_times = []
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pool.trs_pool_reset()
+        r = pool.term_upload(term)
+        pool.trs_normalize(**opts_kw)
+        out = pool.term_download(r)
+        t1 = time.perf_counter()
+        e2e_times.append(t1 - t0)
+        h2d = len(term) * 4 * (4 + prog.maxarity) + 8
+        d2h = st["high_water"] * 4 * (1 + prog.maxarity) + 8
+        assert len(out) == 17712
+    e2e = rewrites / statistics.mean(e2e_times)
+    e2e = reduce_max(0) if False else e2e
+
+    return {
+        "value": value, "ms": ms_max, "stats": st, "mode": mode, "opts": opts_kw,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": nbytes},
+        "plain": {"ms": plain_ms, "value": rewrites / (plain_ms / 1e3),
+                  "sweeps": plain_st["sweeps"], "visits": plain_st["visits"]},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": 2 * args.steps,
+    }
+
+
+def cpu_baseline(target_s=10.0):
+    from oracle import Oracle
+    o = Oracle(ti.FIB)
+    term = ti.fib_term(FIB_N)
+    n, t0 = 0, time.perf_counter()
+    rew = 0
+    while time.perf_counter() - t0 < target_s:
+        r = o.normalize(term)
+        rew += r.rewrites
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": rew / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full normalisations of fib(22) (single-thread leftmost-innermost C oracle)",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="frontier")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, ws, local = dist_init()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(args.warmup):
+            cpu_baseline(0.05)
+        base = None
+        for _ in range(args.steps):
+            base = cpu_baseline(max(0.5, args.cpu_seconds / max(args.steps, 1)))
+            steps.append(base["value"])
+        v = statistics.mean(steps)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 186579 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "engine": "cpu oracle"},
+                "cpu_baseline": dict(base, value=v),
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    r = run_ours(args, rank, ws, local)
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.cpu_seconds)
+    st = r["stats"]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": r["mode"], "driver": r["opts"].get("driver"),
+                   "block_size": r["opts"].get("block_size"), "solo_max": r["opts"].get("solo_max"),
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "time_to_nf_ms": r["ms"], "plain_sweep": r["plain"],
+        "speedup_vs_plain": r["plain"]["ms"] / r["ms"],
+        "sweeps": st["sweeps"], "rewrites": st["rewrites"],
+        "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"],
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

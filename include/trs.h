@@ -1,0 +1,249 @@
+/*
+ * trs.h -- C ABI of the GB300 term-rewriting engine.
+ *
+ * The engine normalises ground terms under a term rewrite system (TRS) with the
+ * parallel innermost method of "Term Rewriting on GPUs" (arxiv 2009.07174):
+ * terms live in a structure-of-arrays node store (head symbol, one index array
+ * per argument position, normal-form stamp, reference count), and repeated
+ * sweeps rewrite, in place, every node that is not in normal form and whose
+ * arguments all are (Sec. 3, the derive kernel), taking new nodes from a free
+ * list or above the high-water mark (Sec. 3, get_new_index) and reclaiming
+ * nodes whose reference count reaches zero (Sec. 3, collect_free_indices),
+ * until a sweep changes nothing.
+ *
+ * Conventions shared by every call:
+ *  - Symbols are int32 ids 1 .. nsym-1; id 0 is the null node index and never
+ *    a symbol.  A variable in a rule is a negative id (-1, -2, ...).
+ *  - A term is the preorder sequence of its symbol ids; arities come from the
+ *    signature, so the sequence determines the tree (Sec. 2, terms).
+ *  - Node indices are int32; index 0 is the null index (Sec. 3, data layout).
+ *  - `trs_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *  - Every call returns a trs_status; TRS_OK is 0.  On failure the call has
+ *    no effect unless stated, and trs_last_error() returns a message for the
+ *    calling thread.
+ *  - Nothing here ever traps or hangs the GPU: device-side failures (pool
+ *    full, sweep limit, a spin-wait that ran out of time) are written to a
+ *    status word and returned by the next synchronising call.
+ */
+#ifndef TRS_H
+#define TRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *trs_stream; /* same type as cudaStream_t */
+
+#define TRS_MAX_ARITY    8     /* largest arity of a symbol */
+#define TRS_MAX_SYMBOLS  4096  /* nsym limit (symbol ids < 4096) */
+#define TRS_MAX_PATTERN  16    /* nodes in one left-hand side */
+#define TRS_MAX_RHS      32    /* nodes in one right-hand side */
+#define TRS_MAX_VARS     16    /* distinct variables in one rule */
+#define TRS_MAX_RULES    1024
+#define TRS_MAX_CAPACITY (1LL << 30) /* node slots in one pool */
+
+typedef enum {
+    TRS_OK = 0,
+    TRS_ERR_ARG = 1,           /* null pointer, bad size or bad option */
+    TRS_ERR_LHS_VAR = 2,       /* a left-hand side is a variable (Def. 1, (1)) */
+    TRS_ERR_RHS_VARS = 3,      /* Var(r) is not a subset of Var(l) (Def. 1, (2)) */
+    TRS_ERR_NONLINEAR = 4,     /* a variable occurs twice in a left-hand side (Sec. 2) */
+    TRS_ERR_ARITY = 5,         /* a preorder sequence does not fit the arities */
+    TRS_ERR_SYMBOL = 6,        /* symbol id 0 or >= nsym */
+    TRS_ERR_MAXARITY = 7,      /* an arity above TRS_MAX_ARITY, or nsym out of range */
+    TRS_ERR_TOO_BIG = 8,       /* a rule or the rule set exceeds the limits above */
+    TRS_ERR_BAD_TERM = 9,      /* an uploaded term is not a well-formed ground term */
+    TRS_ERR_POOL_FULL = 10,    /* the node store ran out of slots */
+    TRS_ERR_SWEEP_LIMIT = 11,  /* max_sweeps reached (e.g. a non-terminating TRS, Sec. 2) */
+    TRS_ERR_TIMEOUT = 12,      /* a device spin-wait exceeded its time limit */
+    TRS_ERR_BUFFER_SMALL = 13, /* output buffer too small; the required size is returned */
+    TRS_ERR_CUDA = 14,         /* a CUDA runtime call failed (message in trs_last_error) */
+    TRS_ERR_STATE = 15,        /* call not valid in the current state (e.g. dead root) */
+    TRS_ERR_NO_PREDICTOR = 16  /* learned mode without an attached, trained predictor */
+} trs_status;
+
+/* Calling thread's message for the last failed call ("" if none). */
+const char *trs_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Rule compilation (host only; never touches the GPU)                       */
+
+/* Signature (Sec. 2): nsym ids, arity[s] for s in 0..nsym-1 (arity[0] ignored). */
+typedef struct {
+    int32_t nsym;
+    const int32_t *arity;
+} trs_signature;
+
+/* One rule l -> r (Def. 1): both sides as preorder id sequences. */
+typedef struct {
+    const int32_t *lhs;
+    int32_t lhs_len;
+    const int32_t *rhs;
+    int32_t rhs_len;
+} trs_rule;
+
+typedef struct trs_program trs_program;
+
+/* Validate and compile a TRS (Def. 1 and the left-linearity assumption of
+ * Sec. 2) into match / construct tables.  Rule order is priority order: for a
+ * head symbol the first matching rule in `rules` is applied (Sec. 2, the
+ * rewrite procedure).  `rules` and `sig` are only read during the call.  The
+ * caller owns *out and frees it with trs_program_free.
+ * Errors: TRS_ERR_ARG, _LHS_VAR, _RHS_VARS, _NONLINEAR, _ARITY, _SYMBOL,
+ * _MAXARITY, _TOO_BIG (with the offending rule in trs_last_error()). */
+int trs_compile(const trs_signature *sig, const trs_rule *rules, int32_t nrules,
+                trs_program **out);
+void trs_program_free(trs_program *prog);
+/* Largest arity of the compiled signature (the number of argument arrays). */
+int32_t trs_program_maxarity(const trs_program *prog);
+
+/* ------------------------------------------------------------------------ */
+/* Node store ("pool")                                                        */
+
+typedef struct trs_pool trs_pool;
+
+/* Device bytes needed for a pool of `capacity` node slots (slot 0 included). */
+int trs_pool_bytes(const trs_program *prog, int64_t capacity, size_t *bytes);
+
+/* Create a pool in caller-owned device memory `dev_mem` (at least
+ * trs_pool_bytes bytes, 256-byte aligned, on the current device).  The pool
+ * keeps `prog` by reference: free the pool before the program.  The memory
+ * stays owned by the caller and must outlive the pool.  Initialisation is
+ * enqueued on `stream`.  Errors: TRS_ERR_ARG, TRS_ERR_CUDA. */
+int trs_pool_create(const trs_program *prog, int64_t capacity, void *dev_mem, size_t bytes,
+                    trs_stream stream, trs_pool **out);
+/* Release host-side state (graphs, staging buffers); not the device memory. */
+void trs_pool_free(trs_pool *pool);
+/* Empty the pool (all slots free, counters zero); enqueued on `stream`. */
+int trs_pool_reset(trs_pool *pool, trs_stream stream);
+
+/* Upload ground terms as trees (no sharing between or inside terms) above the
+ * high-water mark.  flat/offsets: host arrays, nterms terms, term t is
+ * flat[offsets[t] .. offsets[t+1]).  roots_out (host, nterms entries) receives
+ * each term's root index; each root is pinned (reference count 1) until
+ * term_release.  Nodes start not in normal form (Sec. 3: nf is computed by the
+ * sweeps).  Synchronises `stream`; host buffers are only read during the
+ * call.  Errors: TRS_ERR_ARG, TRS_ERR_BAD_TERM (no change made),
+ * TRS_ERR_POOL_FULL (no change made), TRS_ERR_CUDA. */
+int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offsets,
+                      int32_t nterms, int32_t *roots_out, trs_stream stream);
+/* Single-term form of term_upload_batch. */
+int term_upload(trs_pool *pool, const int32_t *preorder, int64_t len, int32_t *root_out,
+                trs_stream stream);
+
+/* Unpin a root; its nodes are reclaimed by a later garbage collection.
+ * Enqueued on `stream`.  Errors: TRS_ERR_ARG. */
+int term_release(trs_pool *pool, int32_t root, trs_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Normalisation                                                              */
+
+typedef enum {
+    TRS_MODE_PLAIN = 0,    /* every sweep visits all slots below the high-water mark
+                              (the topology-driven derive kernel of Sec. 3) */
+    TRS_MODE_FRONTIER = 1, /* every sweep visits only nodes that became ready in the
+                              previous sweep (exact; same sweeps as PLAIN) */
+    TRS_MODE_LEARNED = 2   /* sweeps visit a frontier chosen by the attached predictor
+                              and the nodes the previous sweep touched; a full sweep
+                              confirms termination */
+} trs_mode;
+
+typedef enum {
+    TRS_DRIVER_PERSISTENT = 0, /* one cooperative launch runs every sweep (grid barrier) */
+    TRS_DRIVER_GRAPH = 1,      /* a CUDA graph with a device-side while-loop condition */
+    TRS_DRIVER_HOST = 2        /* one launch per sweep, host reads the loop state back
+                                  each sweep (the main loop of Sec. 3) */
+} trs_driver;
+
+typedef struct {
+    int32_t mode;            /* trs_mode */
+    int32_t driver;          /* trs_driver */
+    int32_t block_size;      /* threads per block: 128, 256, 512 or 1024 */
+    int32_t grid_blocks;     /* 0 = as many as fit (persistent) / 4 per SM (others) */
+    int64_t max_sweeps;      /* TRS_ERR_SWEEP_LIMIT after this many sweeps */
+    int64_t timeout_ns;      /* limit of any one device spin-wait */
+    int32_t gc_min_dead;     /* collect garbage once this many nodes are dead ... */
+    int32_t gc_div;          /* ... and at least high_water / gc_div of them */
+    int32_t solo_max;        /* persistent frontier/learned: frontiers up to this size
+                                run on one block without grid barriers (0 = never) */
+    int32_t graph_unroll;    /* graph driver: sweeps per loop-condition check */
+    int32_t refresh;         /* learned: sweeps between predictor refreshes */
+    float threshold;         /* learned: predicted probability needed to enter the frontier */
+    int32_t trace;           /* 1 = record one trs_sweep_record per sweep */
+    int32_t reserved0;
+    int64_t time_limit_ns;   /* wall-clock limit of the whole call (TRS_ERR_TIMEOUT) */
+    int32_t reserved[4];
+} trs_opts;
+
+/* Fill *opts with defaults (PLAIN, PERSISTENT, 512 threads, spin-wait limit
+ * 10 s, call limit 120 s, ...). */
+void trs_opts_default(trs_opts *opts);
+
+typedef struct {
+    int64_t status;       /* trs_status of the device run */
+    int64_t rewrites;     /* successful rule applications (the paper's rewritten terms) */
+    int64_t nf_marks;     /* nodes found to be in normal form (no rule matched) */
+    int64_t sweeps;       /* sweeps in which something was rewritten or marked */
+    int64_t visits;       /* candidate nodes examined (readiness checks) */
+    int64_t allocs;       /* new nodes created */
+    int64_t frees;        /* nodes reclaimed by garbage collection */
+    int64_t gc_runs;      /* garbage collections */
+    int64_t confirm_sweeps; /* full confirmation sweeps (frontier / learned) */
+    int64_t confirm_found;  /* ready nodes found by confirmation sweeps (frontier: 0) */
+    int64_t refreshes;    /* learned: predictor refreshes */
+    int64_t frontier_peak;/* largest frontier */
+    int64_t high_water;   /* slots in use up to the high-water mark */
+    int64_t live_nodes;   /* live nodes at the end (high_water - free - dead) */
+    int64_t solo_sweeps;  /* sweeps run by one block */
+    int64_t reserved[9];
+} trs_stats;
+
+/* Normalise every live term of the pool.  Enqueued on `stream`.  If `stats`
+ * is non-NULL the call waits for the stream and fills it (its status field is
+ * the device status: TRS_ERR_POOL_FULL, TRS_ERR_SWEEP_LIMIT or
+ * TRS_ERR_TIMEOUT are returned as the call's result too); with NULL the call
+ * returns after enqueueing and trs_pool_stats reads the result later.
+ * Errors: TRS_ERR_ARG, TRS_ERR_NO_PREDICTOR, TRS_ERR_CUDA, and the device
+ * statuses above. */
+int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_stream stream);
+
+/* Wait for `stream` and read the statistics of the last trs_normalize. */
+int trs_pool_stats(trs_pool *pool, trs_stats *stats, trs_stream stream);
+
+/* Canonical serialisation: the preorder of the (unfolded) tree at `root`.
+ * buf: host, cap entries; *len_out receives the length.  If cap is too small
+ * returns TRS_ERR_BUFFER_SMALL and *len_out is the size needed.  Synchronises
+ * `stream`.  Errors: TRS_ERR_ARG, TRS_ERR_STATE (root not live). */
+int term_download(trs_pool *pool, int32_t root, int32_t *buf, int64_t cap, int64_t *len_out,
+                  trs_stream stream);
+/* Batched form: terms of roots[0..nroots) one after another in buf;
+ * offsets_out (nroots + 1 entries) receives the boundaries. */
+int term_download_batch(trs_pool *pool, const int32_t *roots, int32_t nroots, int32_t *buf,
+                        int64_t cap, int64_t *offsets_out, trs_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Per-sweep trace (mirrors the per-step parallelism series of Sec. 4)       */
+
+typedef struct {
+    int64_t sweep;      /* global sweep number */
+    int32_t rewrites;   /* rewrites in this sweep */
+    int32_t nf_marks;   /* nf marks in this sweep */
+    int32_t visits;     /* nodes examined */
+    int32_t allocs;     /* nodes created */
+    int64_t high_water; /* high-water mark after the sweep */
+} trs_sweep_record;
+
+/* Copy the trace of the last trs_normalize (opts.trace = 1) to buf (host).
+ * Records beyond the pool's trace capacity (65536) keep only the last ones.
+ * Synchronises `stream`. */
+int trs_trace_read(trs_pool *pool, trs_sweep_record *buf, int64_t cap, int64_t *n_out,
+                   trs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRS_H */

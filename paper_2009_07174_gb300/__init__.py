@@ -1,0 +1,268 @@
+"""Python binding of the GB300 term-rewriting engine (C ABI in include/trs.h).
+
+Argument marshalling only: every step of normalisation runs in the CUDA
+library `_build/libtrs_gb300.so`.  PyTorch provides the device memory of a pool
+(one uint8 tensor) and the stream (the current torch stream).  Importing the
+package does not need a GPU; there is no CPU fallback: if the library has not
+been built the import fails.
+
+    import paper_2009_07174_gb300 as trs
+    prog = trs.trs_compile(trs_inputs.FIB)
+    pool = trs.Pool(prog, capacity=1 << 20)
+    roots = pool.term_upload_batch(flat, offsets)
+    stats = pool.trs_normalize(mode="frontier")
+    terms = pool.term_download_batch(roots)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["lib", "TrsError", "Program", "Pool", "trs_compile", "Opts", "Stats",
+           "MODES", "DRIVERS", "STATUS"]
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"paper_2009_07174_gb300: CUDA library {LIB_PATH} is not built; run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (there is no CPU fallback)")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+STATUS = {0: "TRS_OK", 1: "TRS_ERR_ARG", 2: "TRS_ERR_LHS_VAR", 3: "TRS_ERR_RHS_VARS",
+          4: "TRS_ERR_NONLINEAR", 5: "TRS_ERR_ARITY", 6: "TRS_ERR_SYMBOL", 7: "TRS_ERR_MAXARITY",
+          8: "TRS_ERR_TOO_BIG", 9: "TRS_ERR_BAD_TERM", 10: "TRS_ERR_POOL_FULL",
+          11: "TRS_ERR_SWEEP_LIMIT", 12: "TRS_ERR_TIMEOUT", 13: "TRS_ERR_BUFFER_SMALL",
+          14: "TRS_ERR_CUDA", 15: "TRS_ERR_STATE", 16: "TRS_ERR_NO_PREDICTOR"}
+CODE = {v: k for k, v in STATUS.items()}
+MODES = {"plain": 0, "frontier": 1, "learned": 2}
+DRIVERS = {"persistent": 0, "graph": 1, "host": 2}
+
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+
+
+class Signature(ctypes.Structure):
+    _fields_ = [("nsym", _i32), ("arity", _vp)]
+
+
+class Rule(ctypes.Structure):
+    _fields_ = [("lhs", _vp), ("lhs_len", _i32), ("rhs", _vp), ("rhs_len", _i32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", _i32), ("driver", _i32), ("block_size", _i32), ("grid_blocks", _i32),
+                ("max_sweeps", _i64), ("timeout_ns", _i64), ("gc_min_dead", _i32),
+                ("gc_div", _i32), ("solo_max", _i32), ("graph_unroll", _i32), ("refresh", _i32),
+                ("threshold", ctypes.c_float), ("trace", _i32), ("reserved0", _i32),
+                ("time_limit_ns", _i64), ("reserved", _i32 * 4)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, _i64) for n in (
+        "status", "rewrites", "nf_marks", "sweeps", "visits", "allocs", "frees", "gc_runs",
+        "confirm_sweeps", "confirm_found", "refreshes", "frontier_peak", "high_water",
+        "live_nodes", "solo_sweeps")] + [("reserved", _i64 * 9)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+
+
+class SweepRecord(ctypes.Structure):
+    _fields_ = [("sweep", _i64), ("rewrites", _i32), ("nf_marks", _i32), ("visits", _i32),
+                ("allocs", _i32), ("high_water", _i64)]
+
+
+def _sig(name, res, *args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_sig("trs_last_error", ctypes.c_char_p)
+_sig("trs_compile", ctypes.c_int, ctypes.POINTER(Signature), ctypes.POINTER(Rule), _i32,
+     ctypes.POINTER(_vp))
+_sig("trs_program_free", None, _vp)
+_sig("trs_program_maxarity", _i32, _vp)
+_sig("trs_pool_bytes", ctypes.c_int, _vp, _i64, ctypes.POINTER(_sz))
+_sig("trs_pool_create", ctypes.c_int, _vp, _i64, _vp, _sz, _vp, ctypes.POINTER(_vp))
+_sig("trs_pool_free", None, _vp)
+_sig("trs_pool_reset", ctypes.c_int, _vp, _vp)
+_sig("term_upload_batch", ctypes.c_int, _vp, _vp, _vp, _i32, _vp, _vp)
+_sig("term_upload", ctypes.c_int, _vp, _vp, _i64, ctypes.POINTER(_i32), _vp)
+_sig("term_release", ctypes.c_int, _vp, _i32, _vp)
+_sig("trs_opts_default", None, ctypes.POINTER(Opts))
+_sig("trs_normalize", ctypes.c_int, _vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), _vp)
+_sig("trs_pool_stats", ctypes.c_int, _vp, ctypes.POINTER(Stats), _vp)
+_sig("term_download", ctypes.c_int, _vp, _i32, _vp, _i64, ctypes.POINTER(_i64), _vp)
+_sig("term_download_batch", ctypes.c_int, _vp, _vp, _i32, _vp, _i64, _vp, _vp)
+_sig("trs_trace_read", ctypes.c_int, _vp, ctypes.POINTER(SweepRecord), _i64,
+     ctypes.POINTER(_i64), _vp)
+
+
+class TrsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib.trs_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+def _check(code, where):
+    if code != 0:
+        raise TrsError(code, where)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+class Program:
+    """A compiled TRS (trs_compile).  Host only; usable without a GPU."""
+
+    def __init__(self, handle, trs):
+        self._h = handle
+        self.trs = trs
+
+    @property
+    def maxarity(self) -> int:
+        return lib.trs_program_maxarity(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.trs_program_free(self._h)
+            self._h = None
+
+
+def trs_compile(trs=None, *, arity=None, rules=None) -> Program:
+    """Compile a TRS given as a trs_inputs.TRS, or as arity + [(lhs, rhs)]
+    preorder int arrays (variables negative)."""
+    if trs is not None:
+        arity = trs.arity
+        rules = trs.rules
+    arity = np.ascontiguousarray(arity, dtype=np.int32)
+    keep = [arity]
+    rarr = (Rule * max(1, len(rules)))()
+    for k, (l, r) in enumerate(rules):
+        l = np.ascontiguousarray(l, dtype=np.int32)
+        r = np.ascontiguousarray(r, dtype=np.int32)
+        keep += [l, r]
+        rarr[k] = Rule(_ptr(l), len(l), _ptr(r), len(r))
+    sig = Signature(len(arity), _ptr(arity))
+    h = _vp()
+    _check(lib.trs_compile(ctypes.byref(sig), rarr, len(rules), ctypes.byref(h)), "trs_compile")
+    return Program(h, trs)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib.trs_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "mode":
+            v = MODES[v] if isinstance(v, str) else v
+        elif k == "driver":
+            v = DRIVERS[v] if isinstance(v, str) else v
+        setattr(o, k, v)
+    return o
+
+
+class Pool:
+    """A node store of `capacity` slots in a torch-allocated device buffer."""
+
+    def __init__(self, program: Program, capacity: int, device=None, stream=None):
+        import torch
+        self.program = program
+        self.capacity = int(capacity)
+        nbytes = _sz()
+        _check(lib.trs_pool_bytes(program._h, self.capacity, ctypes.byref(nbytes)), "trs_pool_bytes")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buffer = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=dev)
+        base = self.buffer.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self._h = _vp()
+        _check(lib.trs_pool_create(program._h, self.capacity, _vp(aligned), nbytes.value,
+                                   _stream(stream), ctypes.byref(self._h)), "trs_pool_create")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.trs_pool_free(self._h)
+            self._h = None
+
+    def trs_pool_reset(self, stream=None):
+        _check(lib.trs_pool_reset(self._h, _stream(stream)), "trs_pool_reset")
+
+    def term_upload_batch(self, flat, offsets, stream=None) -> np.ndarray:
+        flat = np.ascontiguousarray(flat, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        n = len(offsets) - 1
+        roots = np.zeros(max(n, 1), dtype=np.int32)
+        _check(lib.term_upload_batch(self._h, _ptr(flat), _ptr(offsets), n, _ptr(roots),
+                                     _stream(stream)), "term_upload_batch")
+        return roots[:n]
+
+    def term_upload(self, term, stream=None) -> int:
+        t = np.ascontiguousarray(term, dtype=np.int32)
+        root = _i32()
+        _check(lib.term_upload(self._h, _ptr(t), len(t), ctypes.byref(root), _stream(stream)),
+               "term_upload")
+        return int(root.value)
+
+    def term_release(self, root: int, stream=None):
+        _check(lib.term_release(self._h, int(root), _stream(stream)), "term_release")
+
+    def trs_normalize(self, opts: Opts | None = None, stream=None, wait: bool = True, **kw):
+        o = opts if opts is not None else default_opts(**kw)
+        st = Stats()
+        code = lib.trs_normalize(self._h, ctypes.byref(o), ctypes.byref(st) if wait else None,
+                                 _stream(stream))
+        _check(code, "trs_normalize")
+        return st.as_dict() if wait else None
+
+    def trs_pool_stats(self, stream=None) -> dict:
+        st = Stats()
+        _check(lib.trs_pool_stats(self._h, ctypes.byref(st), _stream(stream)), "trs_pool_stats")
+        return st.as_dict()
+
+    def term_download_batch(self, roots, cap: int | None = None, stream=None):
+        roots = np.ascontiguousarray(roots, dtype=np.int32)
+        n = len(roots)
+        cap = int(cap) if cap is not None else 1 << 16
+        offs = np.zeros(n + 1, dtype=np.int64)
+        while True:
+            buf = np.zeros(max(cap, 1), dtype=np.int32)
+            code = lib.term_download_batch(self._h, _ptr(roots), n, _ptr(buf), cap, _ptr(offs),
+                                           _stream(stream))
+            if code == CODE["TRS_ERR_BUFFER_SMALL"]:
+                cap = int(offs[n])
+                continue
+            _check(code, "term_download_batch")
+            return [buf[offs[i]:offs[i + 1]].copy() for i in range(n)]
+
+    def term_download(self, root: int, stream=None) -> np.ndarray:
+        return self.term_download_batch([root], stream=stream)[0]
+
+    def trs_trace_read(self, stream=None):
+        cap = 65536
+        buf = (SweepRecord * cap)()
+        n = _i64()
+        _check(lib.trs_trace_read(self._h, buf, cap, ctypes.byref(n), _stream(stream)),
+               "trs_trace_read")
+        return [(r.sweep, r.rewrites, r.nf_marks, r.visits, r.allocs, r.high_water)
+                for r in buf[:n.value]]
+
+
+def autotune_defaults(mode: str = "frontier") -> dict:
+    """Launch options for `mode`: the autotuner's cached choice for this GPU if
+    one exists (see autotune.py), else built-in defaults."""
+    from . import autotune
+    return autotune.choose(mode)

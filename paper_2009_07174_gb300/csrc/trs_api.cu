@@ -1,0 +1,514 @@
+// trs_api.cu -- the C ABI (include/trs.h): node-store pools in caller-owned
+// device memory, term upload / download, and the three sweep-loop drivers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "trs_engine.h"
+
+namespace trs {
+// trs_kernels.cu
+size_t engine_smem_bytes(const DevPool &P);
+cudaError_t engine_configure(int block, size_t smem, int *blocks_per_sm);
+cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
+                          unsigned long long cond, cudaStream_t stream);
+cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream);
+cudaError_t reset_launch(const DevPool &P, cudaStream_t stream);
+cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
+void *engine_kernel_ptr();
+}  // namespace trs
+
+using namespace trs;
+
+struct GraphCache {
+    bool valid = false;
+    LaunchOpts key{};
+    long long budget = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct trs_pool {
+    const trs_program *prog = nullptr;
+    DevPool d{};
+    void *mem = nullptr;
+    size_t bytes = 0;
+    int device = 0;
+    int num_sms = 0;
+    GraphCache graph;
+    LaunchOpts last{};
+    int last_driver = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t hs, args, rc, nfs, par, pend, ring, fq0, fq1, act, trace, ctl, tab, total;
+};
+
+Layout layout(const Program &p, int64_t cap)
+{
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes); return at; };
+    const size_t slots = (size_t)cap * sizeof(int32_t);
+    L.hs = take(slots);
+    L.args = take(slots * (size_t)std::max(1, p.maxarity));
+    L.rc = take(slots);
+    L.nfs = take(slots);
+    L.par = take(slots);
+    L.pend = take(slots);
+    L.ring = take(slots);
+    L.fq0 = take(slots);
+    L.fq1 = take(slots);
+    L.act = take(slots);
+    L.trace = take(sizeof(trs_sweep_record) * (size_t)kTraceCap);
+    L.ctl = take(sizeof(Ctl));
+    L.tab = take(p.table.size() * sizeof(int32_t));
+    L.total = off;
+    return L;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return TRS_ERR_CUDA;
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+int read_ctl(trs_pool *pool, Ctl *h, cudaStream_t stream)
+{
+    CK(cudaMemcpyAsync(h, pool->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream), "read control block");
+    CK(cudaStreamSynchronize(stream), "stream synchronize");
+    return TRS_OK;
+}
+
+// Validate one ground term in preorder; returns its length or -1.
+bool valid_term(const Program &p, const int32_t *t, int64_t len)
+{
+    if (!t || len <= 0) return false;
+    int64_t need = 1;
+    for (int64_t i = 0; i < len; i++) {
+        if (need == 0) return false;
+        int32_t s = t[i];
+        if (s <= 0 || s >= p.nsym) return false;
+        need += p.arity[s] - 1;
+    }
+    return need == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void trs_opts_default(trs_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = TRS_MODE_PLAIN;
+    o->driver = TRS_DRIVER_PERSISTENT;
+    o->block_size = 512;
+    o->grid_blocks = 0;
+    o->max_sweeps = 1LL << 40;
+    o->timeout_ns = 10LL * 1000 * 1000 * 1000;
+    o->gc_min_dead = 4096;
+    o->gc_div = 8;
+    o->solo_max = 0;
+    o->graph_unroll = 16;
+    o->refresh = 64;
+    o->threshold = 0.5f;
+    o->trace = 0;
+    o->time_limit_ns = 120LL * 1000 * 1000 * 1000;
+}
+
+int trs_pool_bytes(const trs_program *prog, int64_t capacity, size_t *bytes)
+{
+    if (!prog || !bytes || capacity < 2 || capacity > TRS_MAX_CAPACITY) {
+        set_error("trs_pool_bytes: bad argument");
+        return TRS_ERR_ARG;
+    }
+    *bytes = layout(prog->p, capacity).total;
+    return TRS_OK;
+}
+
+int trs_pool_create(const trs_program *prog, int64_t capacity, void *dev_mem, size_t bytes,
+                    trs_stream stream, trs_pool **out)
+{
+    if (!out) { set_error("trs_pool_create: out is NULL"); return TRS_ERR_ARG; }
+    *out = nullptr;
+    if (!prog || !dev_mem || capacity < 2 || capacity > TRS_MAX_CAPACITY ||
+        ((uintptr_t)dev_mem % kAlign) != 0) {
+        set_error("trs_pool_create: bad argument (program, memory, alignment or capacity)");
+        return TRS_ERR_ARG;
+    }
+    const Program &p = prog->p;
+    Layout L = layout(p, capacity);
+    if (bytes < L.total) { set_error("trs_pool_create: memory smaller than trs_pool_bytes"); return TRS_ERR_ARG; }
+    trs_pool *pool = new trs_pool;
+    pool->prog = prog;
+    pool->mem = dev_mem;
+    pool->bytes = bytes;
+    char *b = (char *)dev_mem;
+    DevPool &d = pool->d;
+    d.hs = (int32_t *)(b + L.hs);
+    d.args = (int32_t *)(b + L.args);
+    d.rc = (int32_t *)(b + L.rc);
+    d.nfs = (int32_t *)(b + L.nfs);
+    d.par = (int32_t *)(b + L.par);
+    d.pend = (int32_t *)(b + L.pend);
+    d.ring = (int32_t *)(b + L.ring);
+    d.fq[0] = (int32_t *)(b + L.fq0);
+    d.fq[1] = (int32_t *)(b + L.fq1);
+    d.act = nullptr;
+    d.trace = (trs_sweep_record *)(b + L.trace);
+    d.ctl = (Ctl *)(b + L.ctl);
+    d.tab = (const int32_t *)(b + L.tab);
+    d.cap = capacity;
+    d.ma = p.maxarity;
+    d.tab_words = (int32_t)p.table.size();
+    d.trace_cap = kTraceCap;
+    cudaError_t e = cudaGetDevice(&pool->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pool->num_sms, cudaDevAttrMultiProcessorCount, pool->device);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)d.tab, p.table.data(), p.table.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) { delete pool; return cuda_fail(e, "trs_pool_create"); }
+    *out = pool;
+    int st = trs_pool_reset(pool, stream);
+    if (st != TRS_OK) { delete pool; *out = nullptr; return st; }
+    CK(cudaStreamSynchronize(stream), "trs_pool_create: synchronize");
+    return TRS_OK;
+}
+
+void trs_pool_free(trs_pool *pool)
+{
+    if (!pool) return;
+    if (pool->graph.exec) cudaGraphExecDestroy(pool->graph.exec);
+    if (pool->graph.graph) cudaGraphDestroy(pool->graph.graph);
+    delete pool;
+}
+
+int trs_pool_reset(trs_pool *pool, trs_stream stream)
+{
+    if (!pool) { set_error("trs_pool_reset: pool is NULL"); return TRS_ERR_ARG; }
+    CK(cudaMemsetAsync(pool->d.ctl, 0, sizeof(Ctl), stream), "trs_pool_reset");
+    CK(reset_launch(pool->d, stream), "trs_pool_reset: launch");
+    return TRS_OK;
+}
+
+int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offsets, int32_t nterms,
+                      int32_t *roots_out, trs_stream stream)
+{
+    if (!pool || nterms < 0 || (nterms > 0 && (!flat || !offsets || !roots_out))) {
+        set_error("term_upload_batch: bad argument");
+        return TRS_ERR_ARG;
+    }
+    if (nterms == 0) return TRS_OK;
+    const Program &p = pool->prog->p;
+    const int64_t total = offsets[nterms] - offsets[0];
+    for (int32_t t = 0; t < nterms; t++) {
+        if (offsets[t + 1] < offsets[t] ||
+            !valid_term(p, flat + offsets[t], offsets[t + 1] - offsets[t])) {
+            set_error("term_upload_batch: term " + std::to_string(t) + " is not a ground term");
+            return TRS_ERR_BAD_TERM;
+        }
+    }
+    Ctl h;
+    int st = read_ctl(pool, &h, stream);
+    if (st != TRS_OK) return st;
+    const int64_t base = h.n_top;
+    if (base + total > pool->d.cap) {
+        set_error("term_upload_batch: pool full");
+        return TRS_ERR_POOL_FULL;
+    }
+    const int ma = std::max(1, p.maxarity);
+    std::vector<int32_t> hs(total), rc(total, 1), nfs(total, -(int32_t)h.sweep_id), par(total, 0);
+    std::vector<int32_t> args((size_t)ma * total, 0);
+    struct Open { int64_t node; int32_t next, arity; };
+    std::vector<Open> stk;
+    for (int32_t t = 0; t < nterms; t++) {
+        const int64_t b = offsets[t] - offsets[0];
+        const int64_t len = offsets[t + 1] - offsets[t];
+        stk.clear();
+        for (int64_t q = 0; q < len; q++) {
+            const int32_t s = flat[offsets[t] + q];
+            const int64_t node = b + q;
+            hs[node] = s;
+            if (!stk.empty()) {
+                Open &o = stk.back();
+                args[(size_t)o.next * total + o.node] = (int32_t)(base + node);
+                par[node] = (int32_t)(base + o.node);
+                if (++o.next == o.arity) stk.pop_back();
+            }
+            if (p.arity[s] > 0) stk.push_back({node, 0, p.arity[s]});
+        }
+        roots_out[t] = (int32_t)(base + b);
+    }
+    const size_t sz = (size_t)total * sizeof(int32_t);
+    const DevPool &d = pool->d;
+    CK(cudaMemcpyAsync(d.hs + base, hs.data(), sz, cudaMemcpyHostToDevice, stream), "upload hs");
+    for (int j = 0; j < p.maxarity; j++)
+        CK(cudaMemcpyAsync(d.args + (size_t)j * d.cap + base, args.data() + (size_t)j * total, sz,
+                           cudaMemcpyHostToDevice, stream), "upload args");
+    CK(cudaMemcpyAsync(d.rc + base, rc.data(), sz, cudaMemcpyHostToDevice, stream), "upload rc");
+    CK(cudaMemcpyAsync(d.nfs + base, nfs.data(), sz, cudaMemcpyHostToDevice, stream), "upload nfs");
+    CK(cudaMemcpyAsync(d.par + base, par.data(), sz, cudaMemcpyHostToDevice, stream), "upload par");
+    long long ntop = base + total;
+    CK(cudaMemcpyAsync(&d.ctl->n_top, &ntop, sizeof(ntop), cudaMemcpyHostToDevice, stream), "upload n_top");
+    CK(cudaStreamSynchronize(stream), "upload synchronize");
+    return TRS_OK;
+}
+
+int term_upload(trs_pool *pool, const int32_t *preorder, int64_t len, int32_t *root_out,
+                trs_stream stream)
+{
+    int64_t offs[2] = {0, len};
+    return term_upload_batch(pool, preorder, offs, 1, root_out, stream);
+}
+
+int term_release(trs_pool *pool, int32_t root, trs_stream stream)
+{
+    if (!pool || root <= 0 || root >= pool->d.cap) { set_error("term_release: bad argument"); return TRS_ERR_ARG; }
+    CK(release_launch(pool->d, root, stream), "term_release");
+    return TRS_OK;
+}
+
+static int validate_opts(const trs_opts *o)
+{
+    if (o->mode < 0 || o->mode > 2 || o->driver < 0 || o->driver > 2) return TRS_ERR_ARG;
+    if (o->block_size != 128 && o->block_size != 256 && o->block_size != 512 && o->block_size != 1024)
+        return TRS_ERR_ARG;
+    if (o->max_sweeps <= 0 || o->timeout_ns <= 0 || o->gc_div <= 0 || o->gc_min_dead < 0 ||
+        o->grid_blocks < 0 || o->solo_max < 0 || o->graph_unroll <= 0 || o->time_limit_ns <= 0)
+        return TRS_ERR_ARG;
+    return TRS_OK;
+}
+
+static bool same_key(const LaunchOpts &a, const LaunchOpts &b)
+{
+    return std::memcmp(&a, &b, sizeof(LaunchOpts)) == 0;
+}
+
+// Build (once per launch configuration) a graph whose only node is a while
+// loop around the engine kernel; the kernel clears the loop condition when the
+// normalisation ends or fails.
+static int build_graph(trs_pool *pool, const LaunchOpts &o, long long budget)
+{
+    GraphCache &G = pool->graph;
+    if (G.valid && same_key(G.key, o) && G.budget == budget) return TRS_OK;
+    if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
+    if (G.graph) { cudaGraphDestroy(G.graph); G.graph = nullptr; }
+    G.valid = false;
+    CK(cudaGraphCreate(&G.graph, 0), "graph create");
+    cudaGraphConditionalHandle handle;
+    CK(cudaGraphConditionalHandleCreate(&handle, G.graph, 1, cudaGraphCondAssignDefault), "conditional handle");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    CK(cudaGraphAddNode(&loop, G.graph, nullptr, nullptr, 0, &cp), "conditional node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    DevPool P = pool->d;
+    LaunchOpts lo = o;
+    long long bud = budget;
+    unsigned long long cond = (unsigned long long)handle;
+    void *kargs[4] = {&P, &lo, &bud, &cond};
+    cudaKernelNodeParams kp = {};
+    kp.func = engine_kernel_ptr();
+    kp.gridDim = dim3((unsigned)o.grid);
+    kp.blockDim = dim3((unsigned)o.block);
+    kp.sharedMemBytes = (unsigned)engine_smem_bytes(pool->d);
+    kp.kernelParams = kargs;
+    cudaGraphNode_t kn;
+    CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp), "kernel node");
+    cudaLaunchAttributeValue v = {};
+    v.cooperative = 1;
+    CK(cudaGraphKernelNodeSetAttribute(kn, cudaLaunchAttributeCooperative, &v), "cooperative attribute");
+    CK(cudaGraphInstantiate(&G.exec, G.graph, 0), "graph instantiate");
+    G.key = o;
+    G.budget = budget;
+    G.valid = true;
+    return TRS_OK;
+}
+
+int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_stream stream)
+{
+    if (!pool) { set_error("trs_normalize: pool is NULL"); return TRS_ERR_ARG; }
+    trs_opts o;
+    if (opts) o = *opts;
+    else trs_opts_default(&o);
+    if (validate_opts(&o) != TRS_OK) { set_error("trs_normalize: invalid options"); return TRS_ERR_ARG; }
+    if (o.mode == TRS_MODE_LEARNED) {
+        set_error("trs_normalize: learned mode needs a predictor");
+        return TRS_ERR_NO_PREDICTOR;
+    }
+    const size_t smem = engine_smem_bytes(pool->d);
+    int bps = 0;
+    CK(engine_configure(o.block_size, smem, &bps), "occupancy");
+    if (bps <= 0) { set_error("trs_normalize: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
+    int max_grid = bps * pool->num_sms;
+    int grid = o.grid_blocks > 0 ? std::min(o.grid_blocks, max_grid) : max_grid;
+    LaunchOpts lo{};
+    lo.mode = o.mode;
+    lo.block = o.block_size;
+    lo.grid = grid;
+    lo.gc_min_dead = o.gc_min_dead;
+    lo.gc_div = o.gc_div;
+    lo.solo_max = o.solo_max;
+    lo.trace = o.trace;
+    lo.refresh = o.refresh;
+    lo.threshold = o.threshold;
+    lo.timeout_ns = o.timeout_ns;
+    lo.time_limit_ns = o.time_limit_ns;
+    pool->last = lo;
+    pool->last_driver = o.driver;
+    CK(prep_launch(pool->d.ctl, o.max_sweeps, o.mode != TRS_MODE_PLAIN ? 1 : 0, stream), "prepare");
+    if (o.driver == TRS_DRIVER_PERSISTENT) {
+        CK(engine_launch(pool->d, lo, LLONG_MAX, 0ull, stream), "engine launch");
+    } else if (o.driver == TRS_DRIVER_GRAPH) {
+        int st = build_graph(pool, lo, o.graph_unroll);
+        if (st != TRS_OK) return st;
+        CK(cudaGraphLaunch(pool->graph.exec, stream), "graph launch");
+    } else {
+        // Sec. 3 main loop: launch one sweep, read the loop state back, repeat
+        int hflags[2];
+        for (;;) {
+            CK(engine_launch(pool->d, lo, 1, 0ull, stream), "engine launch");
+            CK(cudaMemcpyAsync(&hflags[0], &pool->d.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, stream),
+               "read done");
+            CK(cudaMemcpyAsync(&hflags[1], &pool->d.ctl->status, sizeof(int), cudaMemcpyDeviceToHost, stream),
+               "read status");
+            CK(cudaStreamSynchronize(stream), "sweep synchronize");
+            if (hflags[0] || hflags[1]) break;
+        }
+    }
+    if (stats) return trs_pool_stats(pool, stats, stream);
+    return TRS_OK;
+}
+
+int trs_pool_stats(trs_pool *pool, trs_stats *s, trs_stream stream)
+{
+    if (!pool || !s) { set_error("trs_pool_stats: bad argument"); return TRS_ERR_ARG; }
+    Ctl h;
+    int st = read_ctl(pool, &h, stream);
+    if (st != TRS_OK) return st;
+    std::memset(s, 0, sizeof(*s));
+    s->status = h.status;
+    s->rewrites = h.st_rewrites;
+    s->nf_marks = h.st_nf_marks;
+    s->sweeps = h.st_sweeps;
+    s->visits = h.st_visits;
+    s->allocs = h.st_allocs;
+    s->frees = h.st_frees;
+    s->gc_runs = h.st_gc_runs;
+    s->confirm_sweeps = h.st_confirm;
+    s->confirm_found = h.st_confirm_found;
+    s->refreshes = h.st_refreshes;
+    s->frontier_peak = h.st_frontier_peak;
+    s->high_water = h.n_top;
+    s->live_nodes = (h.n_top - 1) - (h.fl_end - h.fl_begin) - h.dead;
+    s->solo_sweeps = h.st_solo_sweeps;
+    if (h.status != 0) {
+        set_error(std::string("trs_normalize: device status ") + std::to_string(h.status));
+        return h.status;
+    }
+    return TRS_OK;
+}
+
+int term_download_batch(trs_pool *pool, const int32_t *roots, int32_t nroots, int32_t *buf,
+                        int64_t cap, int64_t *offsets_out, trs_stream stream)
+{
+    if (!pool || nroots < 0 || (nroots > 0 && (!roots || !offsets_out)) || cap < 0 || (cap > 0 && !buf)) {
+        set_error("term_download: bad argument");
+        return TRS_ERR_ARG;
+    }
+    const Program &p = pool->prog->p;
+    Ctl h;
+    int st = read_ctl(pool, &h, stream);
+    if (st != TRS_OK) return st;
+    const int64_t n = h.n_top;
+    const DevPool &d = pool->d;
+    for (int32_t r = 0; r < nroots; r++) {
+        if (roots[r] <= 0 || roots[r] >= n) { set_error("term_download: root out of range"); return TRS_ERR_STATE; }
+        int32_t v[2];
+        CK(cudaMemcpyAsync(&v[0], d.nfs + roots[r], sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "read root");
+        CK(cudaMemcpyAsync(&v[1], d.rc + roots[r], sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "read root");
+        CK(cudaStreamSynchronize(stream), "read root");
+        if (v[0] == 0 || v[1] <= 0) { set_error("term_download: root is not live"); return TRS_ERR_STATE; }
+    }
+    std::vector<int32_t> hs(n);
+    std::vector<int32_t> args((size_t)std::max(1, p.maxarity) * n);
+    CK(cudaMemcpyAsync(hs.data(), d.hs, n * sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "download hs");
+    for (int j = 0; j < p.maxarity; j++)
+        CK(cudaMemcpyAsync(args.data() + (size_t)j * n, d.args + (size_t)j * d.cap, n * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, stream), "download args");
+    CK(cudaStreamSynchronize(stream), "download synchronize");
+    int64_t out = 0;
+    std::vector<int32_t> stk;
+    offsets_out[0] = 0;
+    for (int32_t r = 0; r < nroots; r++) {
+        stk.clear();
+        stk.push_back(roots[r]);
+        while (!stk.empty()) {
+            int32_t x = stk.back();
+            stk.pop_back();
+            if (x <= 0 || x >= n) { set_error("term_download: dangling index"); return TRS_ERR_STATE; }
+            int32_t s = hs[x];
+            if (s <= 0 || s >= p.nsym) { set_error("term_download: corrupt node"); return TRS_ERR_STATE; }
+            if (out < cap) buf[out] = s;
+            out++;
+            for (int a = p.arity[s] - 1; a >= 0; a--) stk.push_back(args[(size_t)a * n + x]);
+        }
+        offsets_out[r + 1] = out;
+    }
+    if (out > cap) {
+        set_error("term_download: buffer too small");
+        return TRS_ERR_BUFFER_SMALL;
+    }
+    return TRS_OK;
+}
+
+int term_download(trs_pool *pool, int32_t root, int32_t *buf, int64_t cap, int64_t *len_out,
+                  trs_stream stream)
+{
+    if (!len_out) { set_error("term_download: len_out is NULL"); return TRS_ERR_ARG; }
+    int64_t offs[2] = {0, 0};
+    int st = term_download_batch(pool, &root, 1, buf, cap, offs, stream);
+    *len_out = offs[1];
+    return st;
+}
+
+int trs_trace_read(trs_pool *pool, trs_sweep_record *buf, int64_t cap, int64_t *n_out, trs_stream stream)
+{
+    if (!pool || !n_out || cap < 0 || (cap > 0 && !buf)) { set_error("trs_trace_read: bad argument"); return TRS_ERR_ARG; }
+    Ctl h;
+    int st = read_ctl(pool, &h, stream);
+    if (st != TRS_OK) return st;
+    int64_t n = std::min<int64_t>(h.trace_n, kTraceCap);
+    int64_t first = h.trace_n - n;
+    int64_t take = std::min(n, cap);
+    std::vector<trs_sweep_record> all(kTraceCap);
+    CK(cudaMemcpyAsync(all.data(), pool->d.trace, sizeof(trs_sweep_record) * kTraceCap,
+                       cudaMemcpyDeviceToHost, stream), "trace read");
+    CK(cudaStreamSynchronize(stream), "trace read");
+    for (int64_t i = 0; i < take; i++) buf[i] = all[(first + i) % kTraceCap];
+    *n_out = n;
+    return TRS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,572 @@
+// trs_device.cuh -- device building blocks of the sweep: staged rule tables,
+// per-node rule dispatch and rewrite, warp-aggregated allocation and frontier
+// pushes, block-scan compaction for garbage collection, and the timed grid
+// barrier.  Included by trs_kernels.cu only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "trs_engine.h"
+
+namespace trs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// memory-model helpers
+__device__ __forceinline__ long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_acqrel_add_u32(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+// Loop-control words are read through L2 (never a stale L1 line).
+__device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ldcg_s64(const long long *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void set_status(Ctl *ctl, int st)
+{
+    atomicCAS(&ctl->status, 0, st);
+}
+
+// Grid-wide barrier for co-resident blocks (cooperative launch).  Every wait is
+// bounded by timeout_ns; on expiry the status word becomes TRS_ERR_TIMEOUT and
+// the barrier returns false, as it does when any block has set an error.
+__device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, long long timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(&ctl->bar_gen);
+        __threadfence();
+        unsigned arrived = atom_acqrel_add_u32(&ctl->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            red_release_add_u32(&ctl->bar_gen, 1u);
+        } else {
+            long long t0 = now_ns();
+            while (ld_acquire_u32(&ctl->bar_gen) == gen) {
+                if (ld_relaxed_s32(&ctl->status) != 0) { ok = 0; break; }
+                if (now_ns() - t0 > timeout_ns) { set_status(ctl, TRS_ERR_TIMEOUT); ok = 0; break; }
+            }
+        }
+        __threadfence();
+        if (ld_relaxed_s32(&ctl->status) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// staged rule table
+struct Tab {
+    const int32_t *w;
+    int off_ar, off_first, off_rules;
+    __device__ __forceinline__ int arity(int s) const { return w[off_ar + s]; }
+    __device__ __forceinline__ int first(int s) const { return w[off_first + s]; }
+    __device__ __forceinline__ const int32_t *rule(int r) const { return w + off_rules + r * kRuleWords; }
+};
+
+__device__ __forceinline__ Tab stage_table(const DevPool &P, int32_t *smem)
+{
+    for (int t = threadIdx.x; t < P.tab_words; t += blockDim.x) smem[t] = P.tab[t];
+    __syncthreads();
+    Tab T;
+    T.w = smem;
+    T.off_ar = smem[4];
+    T.off_first = smem[5];
+    T.off_rules = smem[6];
+    return T;
+}
+
+// ---------------------------------------------------------------------------
+// per-sweep state, identical in every block
+struct State {
+    long long k;     // sweep number
+    long long n;     // high-water mark at the start of the sweep
+    long long fb;    // free ring begin (at sweep start)
+    long long fe;    // free ring end
+    long long dead;  // nodes with count 0 not yet reclaimed
+    long long fsz;   // frontier size
+    long long left;  // sweeps left in this call
+    int cur;         // current frontier buffer
+};
+
+struct Counters {    // per-thread, reduced per block at the end of a phase
+    unsigned long long rewrites, nf_marks, visits, allocs, deaths;
+};
+
+enum { M_PLAIN = 0, M_FRONTIER = 1, M_LEARNED = 2 };
+enum { D_SKIP = -1, D_MARK = -2, D_NONE = -3 };
+
+__device__ __forceinline__ bool is_nf_at(int32_t s, long long k) { return s > 0 && s <= k; }
+
+// Readiness and rule dispatch for node i (Sec. 3, derive kernel: a node is
+// rewritten when it is live, not in normal form and all its arguments are in
+// normal form; the rules of its head are tried in order, Sec. 2).
+// Returns a rule slot, D_MARK (no rule matched: normal form) or D_SKIP.
+// reg[] receives the nodes matched by the pattern of the returned rule.
+__device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i, long long k,
+                                      bool check_ready, int32_t *reg, int32_t &h_out)
+{
+    const long long cap = P.cap;
+    int32_t h = P.hs[i];
+    h_out = h;
+    int ar = T.arity(h);
+    if (check_ready) {
+        int32_t c[TRS_MAX_ARITY];
+#pragma unroll
+        for (int j = 0; j < TRS_MAX_ARITY; j++)
+            if (j < ar) c[j] = P.args[j * cap + i];
+        bool ready = true;
+#pragma unroll
+        for (int j = 0; j < TRS_MAX_ARITY; j++)
+            if (j < ar && !is_nf_at(P.nfs[c[j]], k)) ready = false;
+        if (!ready) return D_SKIP;
+    }
+    int r0 = T.first(h), r1 = T.first(h + 1);
+    for (int r = r0; r < r1; r++) {
+        const int32_t *R = T.rule(r);
+        int npat = R[0] & 0xff;
+        const int32_t *pat = T.w + R[2];
+        reg[0] = i;
+        bool ok = true;
+        for (int q = 1; q < npat; q++) {
+            uint32_t w = (uint32_t)pat[q - 1];
+            int32_t node = P.args[(long long)((w >> 8) & 0xff) * cap + reg[w & 0xff]];
+            reg[q] = node;
+            uint32_t sym = w >> 16;
+            if (sym != 0 && (uint32_t)P.hs[node] != sym) { ok = false; break; }
+        }
+        if (ok) return r;
+    }
+    return D_MARK;
+}
+
+// Warp-aggregated allocation of m new slots per lane (Sec. 3, get_new_index):
+// one atomic per warp on the free-ring claim counter; claims past the slots
+// available in the ring overflow to fresh slots above the high-water mark,
+// again with one atomic per warp.  All 32 lanes must call.
+__device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc *A, int m,
+                                           int32_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    int x = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    int total = __shfl_sync(kFull, x, 31);
+    if (total == 0) return true;
+    int excl = x - m;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&A->fl_claims, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    const long long avail = S.fe - S.fb;
+    long long lo = (long long)base, hi = (long long)base + total;
+    long long fresh_from = lo > avail ? lo : avail;
+    long long wfresh = hi > fresh_from ? hi - fresh_from : 0;
+    unsigned long long fbase = 0;
+    if (lane == 31 && wfresh > 0) fbase = atomicAdd(&A->fresh, (unsigned long long)wfresh);
+    fbase = __shfl_sync(kFull, fbase, 31);
+    bool ok = true;
+    for (int j = 0; j < m; j++) {
+        long long pos = lo + excl + j;
+        int32_t idx;
+        if (pos < avail) {
+            idx = P.ring[(S.fb + pos) % P.cap];
+        } else {
+            long long s = S.n + (long long)fbase + (pos - fresh_from);
+            if (s >= P.cap) { ok = false; idx = 0; }
+            else idx = (int32_t)s;
+        }
+        out[j] = idx;
+    }
+    if (!ok) set_status(P.ctl, TRS_ERR_POOL_FULL);
+    return ok;
+}
+
+// Warp-aggregated append of cnt entries per lane to a frontier buffer.
+__device__ __forceinline__ void warp_push(int32_t *buf, unsigned long long *counter, long long cap,
+                                          int cnt, const int32_t *items, Ctl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    int total = __shfl_sync(kFull, x, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    long long at = (long long)base + (x - cnt);
+    for (int j = 0; j < cnt; j++) {
+        if (at + j < cap) buf[at + j] = items[j];
+        else set_status(ctl, TRS_ERR_POOL_FULL);
+    }
+}
+
+// Apply the decision for node i (rule slot r or D_MARK) in sweep k: rewrite in
+// place (Sec. 3, rewrite listing: the redex slot receives the right-hand side's
+// root, new nodes receive the other non-variable positions, variables are
+// shared; the reference counts of new references are incremented before the
+// consumed arguments are decremented) or record that i is in normal form.
+// Nodes to visit in the next sweep are appended to push[] (frontier modes).
+__device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, int32_t i,
+                                      int32_t h, int r, long long k, const int32_t *reg,
+                                      const int32_t *nw, Counters &C, int32_t *push, int &npush)
+{
+    const long long cap = P.cap;
+    if (r == D_MARK) {
+        P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
+        C.nf_marks++;
+        if (mode == M_FRONTIER) {
+            int32_t p = P.par[i];
+            if (p != 0 && atomicSub(&P.pend[p], 1) == 1) push[npush++] = p;
+        }
+        if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
+        return;
+    }
+    const int32_t *R = T.rule(r);
+    const int nnew = (R[0] >> 8) & 0xff;
+    const int ndelta = (R[0] >> 16) & 0xff;
+    const int rootvar = (R[0] >> 24) & 0xff;
+    const int32_t *build = T.w + R[3];
+    const int32_t *delta = T.w + R[4];
+    const int root_nargs = R[5] & 0xff;
+    const int root_pend = (R[5] >> 8) & 0xff;
+    const int32_t stamp_new = -(int32_t)(k + 1);  // not in normal form, eligible next sweep
+
+    // new nodes
+    int pos = root_nargs;
+    for (int j = 0; j < nnew; j++) {
+        int32_t w0 = build[pos++];
+        int32_t w1 = build[pos++];
+        int32_t sym = w0 & 0xffff, na = w0 >> 16;
+        int32_t parent = (w1 & 0xffff) - 1, pj = w1 >> 16;
+        int32_t x = nw[j];
+        P.hs[x] = sym;
+        for (int a = 0; a < na; a++) {
+            int32_t op = build[pos++];
+            P.args[a * cap + x] = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
+        }
+        P.rc[x] = 1;
+        P.nfs[x] = stamp_new;
+        P.par[x] = parent < 0 ? i : nw[parent];
+        P.pend[x] = pj;
+        if (mode == M_LEARNED || (mode == M_FRONTIER && pj == 0)) push[npush++] = x;
+    }
+    // root that is a variable x: i becomes a copy of x (x is in normal form)
+    int32_t xh = 0, xa = 0;
+    int32_t xc[TRS_MAX_ARITY];
+    if (rootvar) {
+        int32_t x = reg[R[1]];
+        xh = P.hs[x];
+        xa = T.arity(xh);
+        for (int a = 0; a < xa; a++) {
+            xc[a] = P.args[a * cap + x];
+            atomicAdd(&P.rc[xc[a]], 1);
+        }
+    }
+    // net reference changes of matched nodes, positive ones first
+    for (int d = 0; d < ndelta; d++) {
+        int32_t w = delta[d];
+        int32_t q = w & 0xff, dv = w >> 8;
+        int32_t old = atomicAdd(&P.rc[reg[q]], dv);
+        if (dv < 0 && old + dv == 0) C.deaths++;
+    }
+    if (rootvar) {
+        P.hs[i] = xh;
+        for (int a = 0; a < xa; a++) P.args[a * cap + i] = xc[a];
+        P.nfs[i] = (int32_t)(k + 1);
+        if (mode == M_FRONTIER) {
+            int32_t p = P.par[i];
+            if (p != 0 && atomicSub(&P.pend[p], 1) == 1) push[npush++] = p;
+        }
+    } else {
+        P.hs[i] = R[1];
+        for (int a = 0; a < root_nargs; a++) {
+            int32_t op = build[a];
+            P.args[a * cap + i] = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
+        }
+        P.pend[i] = root_pend;
+        if (mode == M_LEARNED || (mode == M_FRONTIER && root_pend == 0)) push[npush++] = i;
+    }
+    if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
+    C.rewrites++;
+    C.allocs += nnew;
+}
+
+// Reduce per-thread counters into the sweep accumulator (one atomic per
+// counter per block).
+__device__ __forceinline__ void flush_counters(Counters &C, Acc *A)
+{
+    __shared__ unsigned long long s_c[5];
+    if (threadIdx.x < 5) s_c[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long v[5] = {C.rewrites, C.nf_marks, C.visits, C.allocs, C.deaths};
+#pragma unroll
+    for (int t = 0; t < 5; t++) {
+        unsigned long long x = v[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_c[t], x);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_c[0]) atomicAdd(&A->rewrites, s_c[0]);
+        if (s_c[1]) atomicAdd(&A->nf_marks, s_c[1]);
+        if (s_c[2]) atomicAdd(&A->visits, s_c[2]);
+        if (s_c[3]) atomicAdd(&A->allocs, s_c[3]);
+        if (s_c[4]) atomicAdd(&A->deaths, s_c[4]);
+    }
+    C = Counters{0, 0, 0, 0, 0};
+}
+
+// One decision + allocation + application + push for every lane of a warp
+// (lane-uniform control flow; `cand` marks lanes with a node to consider).
+__device__ __forceinline__ void process_warp(const DevPool &P, const Tab &T, const State &S,
+                                             Acc *A, int mode, bool cand, bool keep, int32_t i,
+                                             bool check_ready, int32_t *next_buf, Counters &C)
+{
+    int32_t reg[TRS_MAX_PATTERN];
+    int32_t nw[TRS_MAX_RHS];
+    int32_t push[TRS_MAX_RHS + 2];
+    int npush = 0;
+    int d = D_NONE;
+    int32_t h = 0;
+    if (keep) push[npush++] = i;  // learned frontier: not yet eligible, keep it
+    if (cand) {
+        C.visits++;
+        d = decide(P, T, i, S.k, check_ready, reg, h);
+        if (mode == M_LEARNED && d == D_SKIP) push[npush++] = i;  // still waiting: keep it
+    }
+    int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;
+    if (__any_sync(kFull, m > 0)) {
+        if (!warp_alloc(P, S, A, m, nw)) d = D_NONE;
+    }
+    if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, d, S.k, reg, nw, C, push, npush);
+    if (mode != M_PLAIN && __any_sync(kFull, npush > 0))
+        warp_push(next_buf, &A->pushes, P.cap, npush, push, P.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// phases
+
+// Plain sweep: visit every slot below the high-water mark (Sec. 3, derive
+// kernel launched for all n terms).  The stamp array is read as int4 (four
+// slots per lane per load, 512 contiguous bytes per warp).
+__device__ void phase_plain(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                            long long warp0, long long nwarps)
+{
+    Counters C{0, 0, 0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    const long long n = S.n;
+    const long long nchunks = (n + 127) / 128;
+    for (long long ch = warp0; ch < nchunks; ch += nwarps) {
+        long long base = ch * 128 + lane * 4;
+        int4 s4 = make_int4(0, 0, 0, 0);
+        if (base + 3 < n) {
+            s4 = *reinterpret_cast<const int4 *>(P.nfs + base);
+        } else {
+            if (base + 0 < n) s4.x = P.nfs[base + 0];
+            if (base + 1 < n) s4.y = P.nfs[base + 1];
+            if (base + 2 < n) s4.z = P.nfs[base + 2];
+        }
+        int32_t sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        bool any[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) any[t] = sv[t] < 0 && -(long long)sv[t] <= S.k;
+        unsigned ball = __ballot_sync(kFull, any[0] || any[1] || any[2] || any[3]);
+        if (!ball) continue;
+#pragma unroll 1
+        for (int t = 0; t < 4; t++) {
+            if (!__any_sync(kFull, any[t])) continue;
+            process_warp(P, T, S, A, M_PLAIN, any[t], false, (int32_t)(base + t), true, nullptr, C);
+        }
+    }
+    flush_counters(C, A);
+}
+
+// Frontier sweep: visit the entries of the current frontier buffer.
+__device__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
+                               long long warp0, long long nwarps)
+{
+    Counters C{0, 0, 0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    const int32_t *cur = P.fq[S.cur];
+    int32_t *next = P.fq[S.cur ^ 1];
+    const long long nchunks = (S.fsz + 31) / 32;
+    for (long long ch = warp0; ch < nchunks; ch += nwarps) {
+        long long e = ch * 32 + lane;
+        bool cand = false, keep = false;
+        int32_t i = 0;
+        if (e < S.fsz) {
+            i = cur[e];
+            int32_t s = P.nfs[i];
+            // frontier-mode entries are ready by construction; a learned
+            // frontier may hold nodes that are waiting, young or already done
+            if (s < 0) {
+                if (-(long long)s <= S.k) cand = true;
+                else keep = (mode == M_LEARNED);
+            }
+        }
+        if (!__any_sync(kFull, cand || keep)) continue;
+        process_warp(P, T, S, A, mode, cand, keep, i, mode == M_LEARNED, next, C);
+    }
+    flush_counters(C, A);
+}
+
+// Block-wide exclusive scan of one flag per thread; returns the offset of this
+// thread and writes the block total to *total.  Block size <= 1024.
+__device__ __forceinline__ int block_scan_flag(bool f, int *total)
+{
+    __shared__ int s_w[32];
+    __shared__ int s_tot;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    unsigned b = __ballot_sync(kFull, f);
+    int in_warp = __popc(b & ((1u << lane) - 1u));
+    if (lane == 0) s_w[wid] = __popc(b);
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < nw ? s_w[lane] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < nw) s_w[lane] = x - v;
+        if (lane == 31) s_tot = x;
+    }
+    __syncthreads();
+    int off = s_w[wid] + in_warp;
+    *total = s_tot;
+    __syncthreads();
+    return off;
+}
+
+// Garbage collection (Sec. 3, collect_free_indices): every slot whose reference
+// count is 0 and that is not already free releases its arguments and is
+// appended to the free ring.  Appends are compacted with a warp ballot and a
+// block scan, one atomic per block and chunk.  Counts that reach 0 here are
+// reclaimed by a later collection unless the slot's own thread sees them in
+// this pass.
+__device__ void phase_gc(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                         long long block0, long long nblocks)
+{
+    __shared__ unsigned long long s_base;
+    unsigned long long frees = 0, deaths = 0;
+    const long long n = S.n;
+    const long long per = (long long)blockDim.x;
+    const long long nchunks = (n + per - 1) / per;
+    for (long long ch = block0; ch < nchunks; ch += nblocks) {
+        long long i = ch * per + threadIdx.x;
+        bool dead = false;
+        if (i >= 1 && i < n) {
+            int32_t s = P.nfs[i];
+            if (s != 0 && P.rc[i] == 0) dead = true;
+        }
+        if (dead) {
+            int32_t h = P.hs[i];
+            int ar = T.arity(h);
+            for (int a = 0; a < ar; a++) {
+                int32_t c = P.args[a * P.cap + i];
+                if (atomicSub(&P.rc[c], 1) == 1) deaths++;
+            }
+            P.nfs[i] = 0;
+            frees++;
+        }
+        int total = 0;
+        int off = block_scan_flag(dead, &total);
+        if (total > 0) {
+            if (threadIdx.x == 0) s_base = atomicAdd(&A->gc_append, (unsigned long long)total);
+            __syncthreads();
+            if (dead) P.ring[(S.fe + (long long)s_base + off) % P.cap] = (int32_t)i;
+            __syncthreads();
+        }
+    }
+    unsigned long long x = frees, y = deaths;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(kFull, x, o);
+        y += __shfl_down_sync(kFull, y, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (x) atomicAdd(&A->gc_frees, x);
+        if (y) atomicAdd(&A->gc_deaths, y);
+    }
+}
+
+// Seed / confirmation scan (frontier mode): recompute, for every live node not
+// in normal form, how many arguments are not in normal form, and append the
+// nodes with none to the current frontier buffer.  Run at the start of a
+// normalisation and, as the full confirmation sweep, whenever the frontier
+// becomes empty.
+__device__ void phase_seed(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                           long long block0, long long nblocks)
+{
+    __shared__ unsigned long long s_base;
+    int32_t *buf = P.fq[S.cur];
+    const long long n = S.n;
+    const long long per = (long long)blockDim.x;
+    const long long nchunks = (n + per - 1) / per;
+    for (long long ch = block0; ch < nchunks; ch += nblocks) {
+        long long i = ch * per + threadIdx.x;
+        bool ready = false;
+        if (i >= 1 && i < n) {
+            int32_t s = P.nfs[i];
+            if (s < 0) {
+                int32_t h = P.hs[i];
+                int ar = T.arity(h);
+                int cnt = 0;
+                for (int a = 0; a < ar; a++) {
+                    int32_t c = P.args[a * P.cap + i];
+                    if (!is_nf_at(P.nfs[c], S.k)) cnt++;
+                }
+                P.pend[i] = cnt;
+                ready = (cnt == 0) && (-(long long)s <= S.k);
+            }
+        }
+        int total = 0;
+        int off = block_scan_flag(ready, &total);
+        if (total > 0) {
+            if (threadIdx.x == 0) s_base = atomicAdd(&A->conf_found, (unsigned long long)total);
+            __syncthreads();
+            if (ready && (long long)s_base + off < P.cap) buf[s_base + off] = (int32_t)i;
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace trs

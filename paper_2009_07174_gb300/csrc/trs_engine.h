@@ -1,0 +1,155 @@
+// trs_engine.h -- internal definitions shared by the engine's translation units
+// (host compiler, device kernels, C ABI).  Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/trs.h"
+
+#ifdef __CUDACC__
+#define TRS_HD __host__ __device__
+#else
+#define TRS_HD
+#endif
+
+namespace trs {
+
+// ---------------------------------------------------------------------------
+// Compiled rule tables (one int32 word stream, staged into shared memory by
+// every kernel that matches rules).
+//
+//   word 0..7   header: magic, nsym, maxarity, nrules, off_arity, off_first,
+//               off_rules, total words
+//   arity[nsym]
+//   first[nsym+1]        rules of head s are rule slots first[s] .. first[s+1]
+//   rules[nrules][RW]    per rule slot (in head-symbol order, textual order kept)
+//   streams              pattern steps, build program, refcount deltas
+//
+// Rule slot words:
+//   0: npat | nnew << 8 | ndelta << 16 | rootvar << 24
+//   1: root symbol (rootvar == 0) or the match register bound to the root
+//      variable (rootvar == 1)
+//   2: offset of the pattern steps (npat - 1 words)
+//   3: offset of the build program
+//   4: offset of the refcount deltas (ndelta words)
+//   5: root_nargs | root_pend << 8 | original rule index << 16
+//
+// Pattern step for pattern node q (preorder, q >= 1; register q holds the node
+// matched by q, register 0 is the redex itself):
+//   parent register | argpos << 8 | symbol << 16   (symbol 0 = a variable)
+// Build program: root operands (root_nargs words), then per new node j (RHS
+// preorder): [sym | nargs << 16], [parent + 1 | pend << 16], nargs operands.
+// parent is -1 for the redex slot, else the index of the parent new node;
+// pend counts the new-node arguments (they are not in normal form).
+// Operand: index | kind << 16, kind 0 = match register, 1 = new node.
+// Delta: register | delta << 8 (arithmetic shift), positive deltas first
+// (new references are counted before consumed ones are dropped).
+// ---------------------------------------------------------------------------
+constexpr int32_t kTabMagic = 0x54525331;  // "TRS1"
+constexpr int kRuleWords = 6;
+constexpr int kMaxTabWords = 12288;  // 48 KB of shared memory at most
+
+struct Program {
+    int32_t nsym = 0;
+    int32_t maxarity = 0;
+    int32_t nrules = 0;
+    std::vector<int32_t> arity;
+    std::vector<int32_t> table;
+    std::vector<int32_t> rule_orig;  // slot -> original rule index
+    std::vector<uint8_t> has_rules;  // per symbol
+};
+
+// ---------------------------------------------------------------------------
+// Device control block.
+// ---------------------------------------------------------------------------
+struct Acc {  // per-sweep accumulators, triple-buffered by sweep number % 3
+    unsigned long long rewrites, nf_marks, visits, allocs;
+    unsigned long long fl_claims;  // free-ring positions claimed in this sweep
+    unsigned long long fresh;      // slots taken above the high-water mark
+    unsigned long long deaths;     // reference counts that reached zero
+    unsigned long long pushes;     // entries written to the next frontier
+    unsigned long long gc_frees, gc_deaths, gc_append;  // garbage collection
+    unsigned long long conf_found, refresh_sel;
+    unsigned long long pad[3];
+};
+
+struct Ctl {
+    // loop state, valid between launches (written by block 0 at exit)
+    long long sweep_id;   // number of the next sweep (stamps are relative to it)
+    long long n_top;      // high-water mark: slots [1, n_top) have been used
+    long long fl_begin;   // free ring: positions [fl_begin, fl_end) hold free slots
+    long long fl_end;
+    long long dead;       // nodes with reference count 0 not yet reclaimed
+    long long fq_size;    // entries in the current frontier
+    int fq_cur;           // which frontier buffer is current
+    int status;           // trs_status of the device run
+    int done;             // graph / host drivers: loop finished
+    int gc_pending;       // graph / host drivers: collect before the next sweep
+    int mode_phase;       // 1 = seed the frontier at the next launch
+    int solo_flags;       // outcome of the last solo episode: done | gc << 1 | confirm << 2 | stop << 3
+    long long solo_ran;   // sweeps run by the last solo episode
+    long long since_refresh;
+    // statistics of the current trs_normalize
+    long long st_rewrites, st_nf_marks, st_sweeps, st_visits, st_allocs, st_frees;
+    long long st_gc_runs, st_confirm, st_confirm_found, st_refreshes, st_frontier_peak;
+    long long st_solo_sweeps;
+    long long sweeps_left;  // max_sweeps budget of the current call
+    // grid barrier
+    unsigned int bar_count, bar_gen;
+    unsigned int solo_gen, pad1;
+    long long trace_n;
+    long long t_start;      // globaltimer at the start of the current call
+    Acc acc[3];
+};
+
+struct DevPool {
+    int32_t *hs;    // head symbol per slot
+    int32_t *args;  // args[j * cap + i]
+    int32_t *rc;    // reference counts
+    int32_t *nfs;   // >0: in normal form from sweep nfs; <0: not, eligible from
+                    // sweep -nfs; 0: free slot
+    int32_t *par;   // frontier mode: the parent of a node not in normal form
+    int32_t *pend;  // frontier mode: arguments not yet in normal form
+    int32_t *ring;  // free ring, cap entries, position p at ring[p % cap]
+    int32_t *fq[2]; // frontier buffers
+    int32_t *act;   // predictor traces: first sweep a node acted after a sample
+    trs_sweep_record *trace;
+    Ctl *ctl;
+    const int32_t *tab;  // compiled rule table
+    long long cap;
+    int32_t ma;
+    int32_t tab_words;
+    int32_t trace_cap;
+    int32_t pad;
+};
+
+constexpr int kTraceCap = 65536;
+
+struct LaunchOpts {
+    int32_t mode;
+    int32_t block;
+    int32_t grid;
+    int32_t gc_min_dead;
+    int32_t gc_div;
+    int32_t solo_max;
+    int32_t trace;
+    int32_t refresh;
+    float threshold;
+    int32_t pad;
+    long long timeout_ns;
+    long long time_limit_ns;
+};
+
+// compile (host)
+int compile_program(const trs_signature *sig, const trs_rule *rules, int32_t nrules,
+                    Program *out, std::string *err);
+
+void set_error(const std::string &msg);
+
+}  // namespace trs
+
+struct trs_program {
+    trs::Program p;
+};
