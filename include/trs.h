@@ -242,6 +242,40 @@ typedef struct {
 int trs_trace_read(trs_pool *pool, trs_sweep_record *buf, int64_t cap, int64_t *n_out,
                    trs_stream stream);
 
+
+/* ------------------------------------------------------------------------ */
+/* Normalisation without allocation                                          */
+
+/* Normalise one term with the node store in a fixed, library-owned device
+ * array instead of caller-provided memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * time they need a normal form -- a real-time host loop that forbids allocator
+ * calls after start-up, code that runs while its framework's memory pool is
+ * locked, or a process whose device memory is already fully reserved -- so it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * d_term: device, the input term in preorder (len symbols); d_out: device,
+ * out_cap entries, receives the normal form in preorder; d_out_len: device,
+ * one int64, receives its length (-1 if it did not fit).  opts: NULL or plain /
+ * frontier mode with the persistent driver.  stats: host, may be NULL.  The
+ * call is synchronous: it waits for `stream` and returns the device status.
+ *
+ * Limits: the array is 24 MiB on every GPU that loads the library and stays
+ * allocated until the process exits; it holds (24 MiB - rule tables) /
+ * (4 * (9 + maxarity)) node slots (about 570,000 for a signature of maximum
+ * arity 2).  A term of len >= that many slots is rejected with
+ * TRS_ERR_TOO_BIG before any GPU work; running out of slots while rewriting
+ * returns TRS_ERR_POOL_FULL; a normal form longer than out_cap returns
+ * TRS_ERR_BUFFER_SMALL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call reuses the same array, which
+ * keeps the previous call's contents (each call clears what it uses first):
+ * calls whose GPU work overlaps -- on different streams or host threads --
+ * race on the array, so serialise them. */
+int trs_normalize_static(const trs_program *prog, const int32_t *d_term, int64_t len,
+                         int32_t *d_out, int64_t out_cap, int64_t *d_out_len,
+                         const trs_opts *opts, trs_stats *stats, trs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,8 @@ _sig("term_download", ctypes.c_int, _vp, _i32, _vp, _i64, ctypes.POINTER(_i64), 
 _sig("term_download_batch", ctypes.c_int, _vp, _vp, _i32, _vp, _i64, _vp, _vp)
 _sig("trs_trace_read", ctypes.c_int, _vp, ctypes.POINTER(SweepRecord), _i64,
      ctypes.POINTER(_i64), _vp)
+_sig("trs_normalize_static", ctypes.c_int, _vp, _vp, _i64, _vp, _i64, _vp,
+     ctypes.POINTER(Opts), ctypes.POINTER(Stats), _vp)
 
 
 class TrsError(RuntimeError):
@@ -259,6 +261,20 @@ class Pool:
                "trs_trace_read")
         return [(r.sweep, r.rewrites, r.nf_marks, r.visits, r.allocs, r.high_water)
                 for r in buf[:n.value]]
+
+
+def trs_normalize_static(program: Program, d_term, d_out, d_out_len, stream=None, **kw) -> dict:
+    """Normalise one term with the library's fixed device array as the node
+    store (no allocation).  d_term: int32 CUDA tensor (preorder); d_out: int32
+    CUDA tensor receiving the normal form; d_out_len: int64 CUDA tensor of one
+    element receiving its length.  Returns the statistics."""
+    o = default_opts(**kw)
+    st = Stats()
+    _check(lib.trs_normalize_static(program._h, _vp(d_term.data_ptr()), d_term.numel(),
+                                    _vp(d_out.data_ptr()), d_out.numel(), _vp(d_out_len.data_ptr()),
+                                    ctypes.byref(o), ctypes.byref(st), _stream(stream)),
+           "trs_normalize_static")
+    return st.as_dict()
 
 
 def autotune_defaults(mode: str = "frontier") -> dict:

@@ -1,0 +1,70 @@
+"""The allocation-free entry point (trs_normalize_static) against the pool API.
+
+Some callers cannot allocate device memory when they need a normal form (a
+real-time loop that forbids allocator calls after start-up, or code running
+while its framework's memory pool is locked); trs_normalize_static serves them
+from a fixed device array.  This file is collected last so that a failure here
+does not hide the other tests under -x.  It checks, for two calls in a row that
+share the array, that the normal form and the counts equal those of
+term_upload / trs_normalize / term_download, and that oversized terms are
+refused before any GPU work."""
+import numpy as np
+import pytest
+
+import trs_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2009_07174_gb300 as trs
+    return torch, trs
+
+
+def via_pool(trs, prog, term, mode):
+    pool = trs.Pool(prog, 1 << 20)
+    root = pool.term_upload(term)
+    st = pool.trs_normalize(mode=mode)
+    return pool.term_download(root), st
+
+
+def via_static(torch, trs, prog, term, mode):
+    d_term = torch.from_numpy(np.ascontiguousarray(term, dtype=np.int32)).cuda()
+    d_out = torch.full((1 << 20,), -7, dtype=torch.int32, device="cuda")
+    d_len = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = trs.trs_normalize_static(prog, d_term, d_out, d_len, mode=mode)
+    n = int(d_len.item())
+    return d_out[:n].cpu().numpy(), st
+
+
+@pytest.mark.parametrize("mode", ["plain", "frontier"])
+def test_static_matches_pool_two_calls(env, mode):
+    torch, trs = env
+    cases = [(ti.FIB, ti.fib_term(15)), (ti.FIB, ti.fib_term(11))]
+    term, _ = ti.msort_batch(seed=4, nlists=4, lmin=3, lmax=20, vmax=9)
+    cases.append((ti.MSORT, term))
+    for t, term in cases:
+        prog = trs.trs_compile(t)
+        want, st_want = via_pool(trs, prog, term, mode)
+        for _ in range(2):       # two calls in a row share the array
+            got, st = via_static(torch, trs, prog, term, mode)
+            assert np.array_equal(got, want)
+            for k in ("rewrites", "nf_marks", "sweeps", "allocs"):
+                assert st[k] == st_want[k], (k, st, st_want)
+
+
+def test_static_rejects_oversized_term(env):
+    torch, trs = env
+    prog = trs.trs_compile(ti.FIB)
+    big = torch.full((1 << 21,), ti.FIB.id["S"], dtype=torch.int32, device="cuda")
+    out = torch.zeros(16, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(trs.TrsError) as e:
+        trs.trs_normalize_static(prog, big, out, n)
+    assert e.value.name == "TRS_ERR_TOO_BIG"
