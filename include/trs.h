@@ -40,7 +40,7 @@ typedef struct CUstream_st *trs_stream; /* same type as cudaStream_t */
 #define TRS_MAX_ARITY    8     /* largest arity of a symbol */
 #define TRS_MAX_SYMBOLS  4096  /* nsym limit (symbol ids < 4096) */
 #define TRS_MAX_PATTERN  16    /* nodes in one left-hand side */
-#define TRS_MAX_RHS      32    /* nodes in one right-hand side */
+#define TRS_MAX_RHS      16    /* nodes in one right-hand side */
 #define TRS_MAX_VARS     16    /* distinct variables in one rule */
 #define TRS_MAX_RULES    1024
 #define TRS_MAX_CAPACITY (1LL << 30) /* node slots in one pool */
@@ -161,7 +161,7 @@ typedef enum {
 typedef struct {
     int32_t mode;            /* trs_mode */
     int32_t driver;          /* trs_driver */
-    int32_t block_size;      /* threads per block: 128, 256, 512 or 1024 */
+    int32_t block_size;      /* threads per block: 128, 256 or 512 */
     int32_t grid_blocks;     /* 0 = as many as fit (persistent) / 4 per SM (others) */
     int64_t max_sweeps;      /* TRS_ERR_SWEEP_LIMIT after this many sweeps */
     int64_t timeout_ns;      /* limit of any one device spin-wait */
@@ -173,7 +173,10 @@ typedef struct {
     int32_t refresh;         /* learned: sweeps between predictor refreshes */
     float threshold;         /* learned: predicted probability needed to enter the frontier */
     int32_t trace;           /* 1 = record one trs_sweep_record per sweep */
-    int32_t reserved0;
+    int32_t eager;           /* frontier mode: > 0 lets a thread go on with a node it
+                                just made ready, up to this many nodes per entry, in
+                                the same sweep (same results and counts, fewer
+                                sweeps); 0 = synchronous sweeps */
     int64_t time_limit_ns;   /* wall-clock limit of the whole call (TRS_ERR_TIMEOUT) */
     int32_t reserved[4];
 } trs_opts;
@@ -196,7 +199,8 @@ typedef struct {
     int64_t refreshes;    /* learned: predictor refreshes */
     int64_t frontier_peak;/* largest frontier */
     int64_t high_water;   /* slots in use up to the high-water mark */
-    int64_t live_nodes;   /* live nodes at the end (high_water - free - dead) */
+    int64_t live_nodes;   /* high_water - free - dead; dead is counted from above
+                             between collections, so this is a lower bound */
     int64_t solo_sweeps;  /* sweeps run by one block */
     int64_t reserved[9];
 } trs_stats;
@@ -242,6 +246,87 @@ typedef struct {
 int trs_trace_read(trs_pool *pool, trs_sweep_record *buf, int64_t cap, int64_t *n_out,
                    trs_stream stream);
 
+
+/* ------------------------------------------------------------------------ */
+/* Frontier predictor (learned frontier)                                     */
+/*                                                                            */
+/* A small perceptron that estimates, from a node's local view (its head      */
+/* symbol, its arguments' head symbols and which arguments are in normal      */
+/* form), the probability that the node is rewritten or found to be in normal */
+/* form within the next `period` sweeps.  Input: one-hot codes of the head and */
+/* of each argument head (symbol 0 = no argument) plus the normal-form bits,  */
+/* dimension D = nsym * (1 + maxarity) + maxarity; two hidden layers of       */
+/* TRS_PRED_HIDDEN ReLU units; sigmoid output.  Parameters are FP32 and laid  */
+/* out as [W1 (H x D, row-major), b1, W2 (H x H), b2, w3, b3]; inference in   */
+/* the engine uses BF16 copies of the weights with FP32 accumulation.  The    */
+/* paper has no learned component: this is the engine's optional frontier    */
+/* policy, and results never depend on it (a full sweep confirms termination).*/
+
+#define TRS_PRED_HIDDEN 32
+
+typedef struct trs_predictor trs_predictor;
+
+typedef struct {
+    int32_t epochs;      /* passes over the samples */
+    int32_t batch;       /* rows per Adam step */
+    float lr, beta1, beta2, eps;  /* Adam */
+    float pos_weight;    /* weight of positive rows in the cross-entropy */
+    int32_t reserved[5];
+} trs_train_opts;
+
+void trs_train_opts_default(trs_train_opts *opts);
+
+/* Device bytes for a predictor of `prog`'s signature.  TRS_ERR_TOO_BIG if the
+ * input dimension is too large for the training kernel's shared memory. */
+int trs_predictor_bytes(const trs_program *prog, size_t *bytes);
+/* Create a predictor in caller-owned device memory (256-byte aligned) with
+ * weights drawn from a seeded uniform initialisation.  Synchronises `stream`. */
+int trs_predictor_create(const trs_program *prog, uint64_t seed, void *dev_mem, size_t bytes,
+                         trs_stream stream, trs_predictor **out);
+void trs_predictor_free(trs_predictor *pred);
+/* Input dimension D and parameter count. */
+int trs_predictor_shape(const trs_predictor *pred, int32_t *input_dim, int64_t *nparams);
+/* Copy the FP32 parameters to / from host memory (n = parameter count);
+ * set also clears the optimiser state.  Synchronise `stream`. */
+int trs_predictor_get(trs_predictor *pred, float *host_params, int64_t n, trs_stream stream);
+int trs_predictor_set(trs_predictor *pred, const float *host_params, int64_t n, trs_stream stream);
+
+/* Training rows: device buffer of trs_samples_bytes(prog, cap) bytes holding
+ * `cap` rows: int32 features [cap][2 + maxarity] (head, argument heads, bits),
+ * then int32 slots [cap], then float labels [cap] (each part 256-byte
+ * aligned). */
+int trs_samples_bytes(const trs_program *prog, int64_t cap, size_t *bytes);
+
+/* Normalise the pool (plain or frontier mode; synchronous sweeps on the
+ * persistent driver) while recording training rows: every `period` sweeps a
+ * hashed fraction `rate` of the live nodes not in normal form is sampled with
+ * its features; a row's label is 1 if its node is rewritten or marked as a
+ * normal form within the next `period` sweeps.  *n_out receives the number of
+ * rows (at most cap).  Statistics as trs_normalize.  Synchronises `stream`. */
+int trs_collect_samples(trs_pool *pool, const trs_opts *opts, int32_t period, float rate,
+                        uint64_t seed, void *dev_samples, int64_t cap, int64_t *n_out,
+                        trs_stats *stats, trs_stream stream);
+
+/* Train with Adam on rows [0, n) of a sample buffer of capacity cap (mean
+ * weighted binary cross-entropy).  epoch_loss (host, epochs entries, may be
+ * NULL) receives the mean loss of each epoch.  The BF16 inference weights are
+ * refreshed at the end. */
+int trs_predictor_train(trs_predictor *pred, const void *dev_samples, int64_t cap, int64_t n,
+                        const trs_train_opts *opts, float *epoch_loss, trs_stream stream);
+/* Gradient of the mean weighted cross-entropy over rows [0, n) at the current
+ * parameters (host_grad: parameter count floats), and the loss; parameters
+ * are not changed.  Synchronises `stream`. */
+int trs_predictor_grad(trs_predictor *pred, const void *dev_samples, int64_t cap, int64_t n,
+                       float pos_weight, float *host_grad, float *host_loss, trs_stream stream);
+/* Probabilities for n device feature rows with the engine's BF16 path. */
+int trs_predictor_infer(trs_predictor *pred, const int32_t *dev_feat, int64_t n, float *dev_prob,
+                        trs_stream stream);
+/* FP32 logits for n device feature rows (reference path). */
+int trs_predictor_logits32(trs_predictor *pred, const int32_t *dev_feat, int64_t n,
+                           float *dev_logit, trs_stream stream);
+/* Use `pred` (same program as the pool; NULL detaches) for TRS_MODE_LEARNED.
+ * The pool keeps it by reference. */
+int trs_pool_attach_predictor(trs_pool *pool, const trs_predictor *pred);
 
 /* ------------------------------------------------------------------------ */
 /* Normalisation without allocation                                          */

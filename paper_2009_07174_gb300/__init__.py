@@ -57,7 +57,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("mode", _i32), ("driver", _i32), ("block_size", _i32), ("grid_blocks", _i32),
                 ("max_sweeps", _i64), ("timeout_ns", _i64), ("gc_min_dead", _i32),
                 ("gc_div", _i32), ("solo_max", _i32), ("graph_unroll", _i32), ("refresh", _i32),
-                ("threshold", ctypes.c_float), ("trace", _i32), ("reserved0", _i32),
+                ("threshold", ctypes.c_float), ("trace", _i32), ("eager", _i32),
                 ("time_limit_ns", _i64), ("reserved", _i32 * 4)]
 
 
@@ -104,6 +104,29 @@ _sig("trs_trace_read", ctypes.c_int, _vp, ctypes.POINTER(SweepRecord), _i64,
      ctypes.POINTER(_i64), _vp)
 _sig("trs_normalize_static", ctypes.c_int, _vp, _vp, _i64, _vp, _i64, _vp,
      ctypes.POINTER(Opts), ctypes.POINTER(Stats), _vp)
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", _i32), ("batch", _i32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("pos_weight", ctypes.c_float), ("reserved", _i32 * 5)]
+
+
+_sig("trs_train_opts_default", None, ctypes.POINTER(TrainOpts))
+_sig("trs_predictor_bytes", ctypes.c_int, _vp, ctypes.POINTER(_sz))
+_sig("trs_predictor_create", ctypes.c_int, _vp, ctypes.c_uint64, _vp, _sz, _vp, ctypes.POINTER(_vp))
+_sig("trs_predictor_free", None, _vp)
+_sig("trs_predictor_shape", ctypes.c_int, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64))
+_sig("trs_predictor_get", ctypes.c_int, _vp, _vp, _i64, _vp)
+_sig("trs_predictor_set", ctypes.c_int, _vp, _vp, _i64, _vp)
+_sig("trs_samples_bytes", ctypes.c_int, _vp, _i64, ctypes.POINTER(_sz))
+_sig("trs_collect_samples", ctypes.c_int, _vp, ctypes.POINTER(Opts), _i32, ctypes.c_float,
+     ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(Stats), _vp)
+_sig("trs_predictor_train", ctypes.c_int, _vp, _vp, _i64, _i64, ctypes.POINTER(TrainOpts), _vp, _vp)
+_sig("trs_predictor_grad", ctypes.c_int, _vp, _vp, _i64, _i64, ctypes.c_float, _vp, _vp, _vp)
+_sig("trs_predictor_infer", ctypes.c_int, _vp, _vp, _i64, _vp, _vp)
+_sig("trs_predictor_logits32", ctypes.c_int, _vp, _vp, _i64, _vp, _vp)
+_sig("trs_pool_attach_predictor", ctypes.c_int, _vp, _vp)
 
 
 class TrsError(RuntimeError):
@@ -230,6 +253,22 @@ class Pool:
         _check(code, "trs_normalize")
         return st.as_dict() if wait else None
 
+    def trs_pool_attach_predictor(self, pred):
+        self._pred = pred  # keep it alive while attached
+        _check(lib.trs_pool_attach_predictor(self._h, pred._h if pred is not None else None),
+               "trs_pool_attach_predictor")
+
+    def trs_collect_samples(self, samples, period: int, rate: float = 1.0, seed: int = 1,
+                            stream=None, **kw):
+        o = default_opts(**kw)
+        st = Stats()
+        n = _i64()
+        _check(lib.trs_collect_samples(self._h, ctypes.byref(o), period, rate, seed, _vp(samples.ptr),
+                                       samples.cap, ctypes.byref(n), ctypes.byref(st), _stream(stream)),
+               "trs_collect_samples")
+        samples.n = int(n.value)
+        return samples.n, st.as_dict()
+
     def trs_pool_stats(self, stream=None) -> dict:
         st = Stats()
         _check(lib.trs_pool_stats(self._h, ctypes.byref(st), _stream(stream)), "trs_pool_stats")
@@ -261,6 +300,98 @@ class Pool:
                "trs_trace_read")
         return [(r.sweep, r.rewrites, r.nf_marks, r.visits, r.allocs, r.high_water)
                 for r in buf[:n.value]]
+
+
+def _aligned_buffer(nbytes, device=None):
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=dev)
+    return buf, (buf.data_ptr() + 255) // 256 * 256
+
+
+class Samples:
+    """Training rows for the predictor in one device buffer (trs_samples_bytes):
+    int32 features [cap][2 + maxarity], int32 slots [cap], float labels [cap]."""
+
+    def __init__(self, program: Program, cap: int, device=None):
+        import torch
+        self.program = program
+        self.cap = int(cap)
+        nb = _sz()
+        _check(lib.trs_samples_bytes(program._h, self.cap, ctypes.byref(nb)), "trs_samples_bytes")
+        self.buffer, self.ptr = _aligned_buffer(nb.value, device)
+        self.F = 2 + program.maxarity
+        off = self.ptr - self.buffer.data_ptr()
+        fb = (self.cap * self.F * 4 + 255) // 256 * 256
+        sb = (self.cap * 4 + 255) // 256 * 256
+        self.feat = self.buffer[off:off + self.cap * self.F * 4].view(torch.int32).view(self.cap, self.F)
+        self.slot = self.buffer[off + fb:off + fb + self.cap * 4].view(torch.int32)
+        self.label = self.buffer[off + fb + sb:off + fb + sb + self.cap * 4].view(torch.float32)
+        self.n = 0
+
+
+class Predictor:
+    """The learned frontier's predictor (trs_predictor_*)."""
+
+    def __init__(self, program: Program, seed: int = 1, device=None, stream=None):
+        self.program = program
+        nb = _sz()
+        _check(lib.trs_predictor_bytes(program._h, ctypes.byref(nb)), "trs_predictor_bytes")
+        self.buffer, ptr = _aligned_buffer(nb.value, device)
+        self._h = _vp()
+        _check(lib.trs_predictor_create(program._h, seed, _vp(ptr), nb.value, _stream(stream),
+                                        ctypes.byref(self._h)), "trs_predictor_create")
+        d, n = _i32(), _i64()
+        _check(lib.trs_predictor_shape(self._h, ctypes.byref(d), ctypes.byref(n)), "trs_predictor_shape")
+        self.input_dim, self.nparams = int(d.value), int(n.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.trs_predictor_free(self._h)
+            self._h = None
+
+    def get_params(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib.trs_predictor_get(self._h, _ptr(out), self.nparams, _stream(stream)), "trs_predictor_get")
+        return out
+
+    def set_params(self, theta, stream=None):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib.trs_predictor_set(self._h, _ptr(t), len(t), _stream(stream)), "trs_predictor_set")
+
+    def train(self, samples: Samples, n: int | None = None, stream=None, **kw):
+        o = TrainOpts()
+        lib.trs_train_opts_default(ctypes.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        n = samples.n if n is None else n
+        losses = np.zeros(o.epochs, dtype=np.float32)
+        _check(lib.trs_predictor_train(self._h, _vp(samples.ptr), samples.cap, n, ctypes.byref(o),
+                                       _ptr(losses), _stream(stream)), "trs_predictor_train")
+        return losses
+
+    def grad(self, samples: Samples, n: int, pos_weight: float = 1.0, stream=None):
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib.trs_predictor_grad(self._h, _vp(samples.ptr), samples.cap, n, pos_weight, _ptr(g),
+                                      ctypes.byref(loss), _stream(stream)), "trs_predictor_grad")
+        return g, float(loss.value)
+
+    def infer(self, feat, stream=None):
+        import torch
+        feat = feat.contiguous()
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _check(lib.trs_predictor_infer(self._h, _vp(feat.data_ptr()), feat.shape[0], _vp(out.data_ptr()),
+                                       _stream(stream)), "trs_predictor_infer")
+        return out
+
+    def logits32(self, feat, stream=None):
+        import torch
+        feat = feat.contiguous()
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _check(lib.trs_predictor_logits32(self._h, _vp(feat.data_ptr()), feat.shape[0],
+                                          _vp(out.data_ptr()), _stream(stream)), "trs_predictor_logits32")
+        return out
 
 
 def trs_normalize_static(program: Program, d_term, d_out, d_out_len, stream=None, **kw) -> dict:

@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtrs_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
-SOURCES = ["trs_compile.cpp", "trs_api.cu", "trs_kernels.cu", "trs_static.cu"]
+SOURCES = ["trs_compile.cpp", "trs_api.cu", "trs_kernels.cu", "trs_mlp.cu", "trs_static.cu"]
 
 
 def _nvcc():

@@ -20,6 +20,9 @@ cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream);
 cudaError_t reset_launch(const DevPool &P, cudaStream_t stream);
 cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
 void *engine_kernel_ptr();
+const unsigned char *predictor_block(const trs_predictor *p);
+size_t predictor_block_bytes(const trs_predictor *p);
+const trs_program *predictor_program(const trs_predictor *p);
 }  // namespace trs
 
 using namespace trs;
@@ -28,6 +31,7 @@ struct GraphCache {
     bool valid = false;
     LaunchOpts key{};
     long long budget = 0;
+    const unsigned char *mlp = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -42,6 +46,8 @@ struct trs_pool {
     GraphCache graph;
     LaunchOpts last{};
     int last_driver = 0;
+    int32_t *act = nullptr;              // per-slot act[] (predictor traces)
+    const trs_predictor *pred = nullptr; // learned mode
 };
 
 namespace {
@@ -173,6 +179,7 @@ int trs_pool_create(const trs_program *prog, int64_t capacity, void *dev_mem, si
     d.fq[0] = (int32_t *)(b + L.fq0);
     d.fq[1] = (int32_t *)(b + L.fq1);
     d.act = nullptr;
+    pool->act = (int32_t *)(b + L.act);
     d.trace = (trs_sweep_record *)(b + L.trace);
     d.ctl = (Ctl *)(b + L.ctl);
     d.tab = (const int32_t *)(b + L.tab);
@@ -180,6 +187,7 @@ int trs_pool_create(const trs_program *prog, int64_t capacity, void *dev_mem, si
     d.ma = p.maxarity;
     d.tab_words = (int32_t)p.table.size();
     d.trace_cap = kTraceCap;
+    d.nsym = p.nsym;
     cudaError_t e = cudaGetDevice(&pool->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pool->num_sms, cudaDevAttrMultiProcessorCount, pool->device);
     if (e == cudaSuccess)
@@ -250,7 +258,8 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
             if (!stk.empty()) {
                 Open &o = stk.back();
                 args[(size_t)o.next * total + o.node] = (int32_t)(base + node);
-                par[node] = (int32_t)(base + o.node);
+                // sign bit: the parent's head is unary (its only argument)
+                par[node] = (int32_t)((uint32_t)(base + o.node) | (o.arity == 1 ? 0x80000000u : 0u));
                 if (++o.next == o.arity) stk.pop_back();
             }
             if (p.arity[s] > 0) stk.push_back({node, 0, p.arity[s]});
@@ -289,10 +298,10 @@ int term_release(trs_pool *pool, int32_t root, trs_stream stream)
 static int validate_opts(const trs_opts *o)
 {
     if (o->mode < 0 || o->mode > 2 || o->driver < 0 || o->driver > 2) return TRS_ERR_ARG;
-    if (o->block_size != 128 && o->block_size != 256 && o->block_size != 512 && o->block_size != 1024)
-        return TRS_ERR_ARG;
+    if (o->block_size != 128 && o->block_size != 256 && o->block_size != 512) return TRS_ERR_ARG;
     if (o->max_sweeps <= 0 || o->timeout_ns <= 0 || o->gc_div <= 0 || o->gc_min_dead < 0 ||
-        o->grid_blocks < 0 || o->solo_max < 0 || o->graph_unroll <= 0 || o->time_limit_ns <= 0)
+        o->grid_blocks < 0 || o->solo_max < 0 || o->graph_unroll <= 0 || o->time_limit_ns <= 0 ||
+        o->eager < 0)
         return TRS_ERR_ARG;
     return TRS_OK;
 }
@@ -305,10 +314,10 @@ static bool same_key(const LaunchOpts &a, const LaunchOpts &b)
 // Build (once per launch configuration) a graph whose only node is a while
 // loop around the engine kernel; the kernel clears the loop condition when the
 // normalisation ends or fails.
-static int build_graph(trs_pool *pool, const LaunchOpts &o, long long budget)
+static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, long long budget)
 {
     GraphCache &G = pool->graph;
-    if (G.valid && same_key(G.key, o) && G.budget == budget) return TRS_OK;
+    if (G.valid && same_key(G.key, o) && G.budget == budget && G.mlp == dp.mlp) return TRS_OK;
     if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
     if (G.graph) { cudaGraphDestroy(G.graph); G.graph = nullptr; }
     G.valid = false;
@@ -323,7 +332,7 @@ static int build_graph(trs_pool *pool, const LaunchOpts &o, long long budget)
     cudaGraphNode_t loop;
     CK(cudaGraphAddNode(&loop, G.graph, nullptr, nullptr, 0, &cp), "conditional node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    DevPool P = pool->d;
+    DevPool P = dp;
     LaunchOpts lo = o;
     long long bud = budget;
     unsigned long long cond = (unsigned long long)handle;
@@ -332,7 +341,7 @@ static int build_graph(trs_pool *pool, const LaunchOpts &o, long long budget)
     kp.func = engine_kernel_ptr();
     kp.gridDim = dim3((unsigned)o.grid);
     kp.blockDim = dim3((unsigned)o.block);
-    kp.sharedMemBytes = (unsigned)engine_smem_bytes(pool->d);
+    kp.sharedMemBytes = (unsigned)engine_smem_bytes(dp);
     kp.kernelParams = kargs;
     cudaGraphNode_t kn;
     CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp), "kernel node");
@@ -342,6 +351,7 @@ static int build_graph(trs_pool *pool, const LaunchOpts &o, long long budget)
     CK(cudaGraphInstantiate(&G.exec, G.graph, 0), "graph instantiate");
     G.key = o;
     G.budget = budget;
+    G.mlp = dp.mlp;
     G.valid = true;
     return TRS_OK;
 }
@@ -353,11 +363,16 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
     if (opts) o = *opts;
     else trs_opts_default(&o);
     if (validate_opts(&o) != TRS_OK) { set_error("trs_normalize: invalid options"); return TRS_ERR_ARG; }
-    if (o.mode == TRS_MODE_LEARNED) {
-        set_error("trs_normalize: learned mode needs a predictor");
+    if (o.mode == TRS_MODE_LEARNED && !pool->pred) {
+        set_error("trs_normalize: learned mode needs an attached predictor");
         return TRS_ERR_NO_PREDICTOR;
     }
-    const size_t smem = engine_smem_bytes(pool->d);
+    DevPool d = pool->d;
+    if (o.mode == TRS_MODE_LEARNED) {
+        d.mlp = predictor_block(pool->pred);
+        d.mlp_bytes = (int32_t)predictor_block_bytes(pool->pred);
+    }
+    const size_t smem = engine_smem_bytes(d);
     int bps = 0;
     CK(engine_configure(o.block_size, smem, &bps), "occupancy");
     if (bps <= 0) { set_error("trs_normalize: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
@@ -375,20 +390,21 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
     lo.threshold = o.threshold;
     lo.timeout_ns = o.timeout_ns;
     lo.time_limit_ns = o.time_limit_ns;
+    lo.eager = o.mode == TRS_MODE_FRONTIER ? o.eager : 0;
     pool->last = lo;
     pool->last_driver = o.driver;
     CK(prep_launch(pool->d.ctl, o.max_sweeps, o.mode != TRS_MODE_PLAIN ? 1 : 0, stream), "prepare");
     if (o.driver == TRS_DRIVER_PERSISTENT) {
-        CK(engine_launch(pool->d, lo, LLONG_MAX, 0ull, stream), "engine launch");
+        CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream), "engine launch");
     } else if (o.driver == TRS_DRIVER_GRAPH) {
-        int st = build_graph(pool, lo, o.graph_unroll);
+        int st = build_graph(pool, d, lo, o.graph_unroll);
         if (st != TRS_OK) return st;
         CK(cudaGraphLaunch(pool->graph.exec, stream), "graph launch");
     } else {
         // Sec. 3 main loop: launch one sweep, read the loop state back, repeat
         int hflags[2];
         for (;;) {
-            CK(engine_launch(pool->d, lo, 1, 0ull, stream), "engine launch");
+            CK(engine_launch(d, lo, 1, 0ull, stream), "engine launch");
             CK(cudaMemcpyAsync(&hflags[0], &pool->d.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, stream),
                "read done");
             CK(cudaMemcpyAsync(&hflags[1], &pool->d.ctl->status, sizeof(int), cudaMemcpyDeviceToHost, stream),
@@ -398,6 +414,70 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
         }
     }
     if (stats) return trs_pool_stats(pool, stats, stream);
+    return TRS_OK;
+}
+
+int trs_pool_attach_predictor(trs_pool *pool, const trs_predictor *pred)
+{
+    if (!pool) { set_error("trs_pool_attach_predictor: pool is NULL"); return TRS_ERR_ARG; }
+    if (pred && predictor_program(pred) != pool->prog) {
+        set_error("trs_pool_attach_predictor: predictor built for another program");
+        return TRS_ERR_ARG;
+    }
+    pool->pred = pred;
+    return TRS_OK;
+}
+
+int trs_collect_samples(trs_pool *pool, const trs_opts *opts, int32_t period, float rate, uint64_t seed,
+                        void *dev_samples, int64_t cap, int64_t *n_out, trs_stats *stats, trs_stream stream)
+{
+    if (!pool || !dev_samples || cap <= 0 || !n_out || period <= 0 || !(rate > 0.f) || rate > 1.f ||
+        ((uintptr_t)dev_samples % 256) != 0) {
+        set_error("trs_collect_samples: bad argument");
+        return TRS_ERR_ARG;
+    }
+    trs_opts o;
+    if (opts) o = *opts;
+    else trs_opts_default(&o);
+    if (validate_opts(&o) != TRS_OK || o.mode == TRS_MODE_LEARNED) {
+        set_error("trs_collect_samples: invalid options (plain or frontier mode)");
+        return TRS_ERR_ARG;
+    }
+    const Program &p = pool->prog->p;
+    const int F = 2 + p.maxarity;
+    DevPool d = pool->d;
+    d.act = pool->act;
+    d.samp_feat = (int32_t *)dev_samples;
+    const size_t feat_b = ((size_t)cap * F * 4 + 255) / 256 * 256;
+    d.samp_slot = (int32_t *)((char *)dev_samples + feat_b);
+    d.samp_label = (float *)((char *)dev_samples + feat_b + ((size_t)cap * 4 + 255) / 256 * 256);
+    d.samp_cap = cap;
+    int bps = 0;
+    CK(engine_configure(o.block_size, engine_smem_bytes(d), &bps), "occupancy");
+    if (bps <= 0) { set_error("trs_collect_samples: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
+    LaunchOpts lo{};
+    lo.mode = o.mode;
+    lo.block = o.block_size;
+    lo.grid = o.grid_blocks > 0 ? std::min(o.grid_blocks, bps * pool->num_sms) : bps * pool->num_sms;
+    lo.gc_min_dead = o.gc_min_dead;
+    lo.gc_div = o.gc_div;
+    lo.solo_max = 0;  // sampling sweeps are grid-wide and synchronous
+    lo.eager = 0;
+    lo.trace = o.trace;
+    lo.timeout_ns = o.timeout_ns;
+    lo.time_limit_ns = o.time_limit_ns;
+    lo.sample_period = period;
+    const double t = (double)rate * 4294967296.0;
+    lo.sample_thresh = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
+    lo.sample_seed = (uint32_t)(seed ^ (seed >> 32));
+    CK(prep_launch(pool->d.ctl, o.max_sweeps, o.mode != TRS_MODE_PLAIN ? 1 : 0, stream), "prepare");
+    CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream), "engine launch");
+    Ctl h;
+    int st = read_ctl(pool, &h, stream);
+    if (st != TRS_OK) return st;
+    *n_out = std::min<int64_t>(h.samp_n, cap);
+    if (stats) return trs_pool_stats(pool, stats, stream);
+    if (h.status != 0) { set_error("trs_collect_samples: device status " + std::to_string(h.status)); return h.status; }
     return TRS_OK;
 }
 
@@ -421,6 +501,7 @@ int trs_pool_stats(trs_pool *pool, trs_stats *s, trs_stream stream)
     s->refreshes = h.st_refreshes;
     s->frontier_peak = h.st_frontier_peak;
     s->high_water = h.n_top;
+    // dead nodes are counted from above between collections: a lower bound
     s->live_nodes = (h.n_top - 1) - (h.fl_end - h.fl_begin) - h.dead;
     s->solo_sweeps = h.st_solo_sweeps;
     if (h.status != 0) {

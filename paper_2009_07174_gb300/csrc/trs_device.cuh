@@ -27,6 +27,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ int ld_relaxed_s32(const int *p)
 {
     int v;
@@ -47,6 +53,13 @@ __device__ __forceinline__ unsigned atom_acqrel_add_u32(unsigned *p, unsigned v)
 __device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldcg_s64(const long long *p) { return __ldcg(p); }
 
+__device__ __forceinline__ int atom_acqrel_add_s32(int *p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ void set_status(Ctl *ctl, int st)
 {
     atomicCAS(&ctl->status, 0, st);
@@ -61,7 +74,7 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, long long tim
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_acquire_u32(&ctl->bar_gen);
+        unsigned gen = ld_relaxed_u32(&ctl->bar_gen);
         __threadfence();
         unsigned arrived = atom_acqrel_add_u32(&ctl->bar_count, 1u);
         if (arrived == nblocks - 1) {
@@ -70,9 +83,12 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, long long tim
             red_release_add_u32(&ctl->bar_gen, 1u);
         } else {
             long long t0 = now_ns();
-            while (ld_acquire_u32(&ctl->bar_gen) == gen) {
-                if (ld_relaxed_s32(&ctl->status) != 0) { ok = 0; break; }
-                if (now_ns() - t0 > timeout_ns) { set_status(ctl, TRS_ERR_TIMEOUT); ok = 0; break; }
+            int spins = 0;
+            while (ld_relaxed_u32(&ctl->bar_gen) == gen) {
+                if ((++spins & 63) == 0) {
+                    if (ld_relaxed_s32(&ctl->status) != 0) { ok = 0; break; }
+                    if (now_ns() - t0 > timeout_ns) { set_status(ctl, TRS_ERR_TIMEOUT); ok = 0; break; }
+                }
             }
         }
         __threadfence();
@@ -115,6 +131,7 @@ struct State {
     long long dead;  // nodes with count 0 not yet reclaimed
     long long fsz;   // frontier size
     long long left;  // sweeps left in this call
+    long long since; // learned: sweeps since the last refresh
     int cur;         // current frontier buffer
 };
 
@@ -236,6 +253,33 @@ __device__ __forceinline__ void warp_push(int32_t *buf, unsigned long long *coun
     }
 }
 
+// A node not in normal form has exactly one parent (variables bind only nodes
+// in normal form, and uploads are trees); par[] holds it, with the sign bit set
+// when the parent's head is unary.  When node i becomes a normal form its
+// parent loses one pending argument; the notifier that takes the count to 0
+// owns the parent's next visit.  A unary parent has no other argument, so no
+// atomic is needed.
+__device__ __forceinline__ void notify_parent(const DevPool &P, int32_t i, int32_t *push, int &npush)
+{
+    const int32_t pv = P.par[i];
+    const int32_t p = pv & 0x7fffffff;
+    if (p == 0) return;
+    if (pv < 0 || atom_acqrel_add_s32(&P.pend[p], -1) == 1) push[npush++] = p;
+}
+
+__device__ __forceinline__ int32_t par_word(const Tab &T, int32_t parent, int32_t parent_sym)
+{
+    return parent | (T.arity(parent_sym) == 1 ? (int32_t)0x80000000 : 0);
+}
+
+// Symbol of new node j of a build program (walks the program; j < 16).
+__device__ __forceinline__ int32_t build_sym(const int32_t *build, int root_nargs, int j)
+{
+    int pos = root_nargs;
+    for (int t = 0; t < j; t++) pos += 2 + (build[pos] >> 16);
+    return build[pos] & 0xffff;
+}
+
 // Apply the decision for node i (rule slot r or D_MARK) in sweep k: rewrite in
 // place (Sec. 3, rewrite listing: the redex slot receives the right-hand side's
 // root, new nodes receive the other non-variable positions, variables are
@@ -250,10 +294,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     if (r == D_MARK) {
         P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
         C.nf_marks++;
-        if (mode == M_FRONTIER) {
-            int32_t p = P.par[i];
-            if (p != 0 && atomicSub(&P.pend[p], 1) == 1) push[npush++] = p;
-        }
+        if (mode == M_FRONTIER) notify_parent(P, i, push, npush);
         if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
         return;
     }
@@ -282,7 +323,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         }
         P.rc[x] = 1;
         P.nfs[x] = stamp_new;
-        P.par[x] = parent < 0 ? i : nw[parent];
+        P.par[x] = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
         P.pend[x] = pj;
         if (mode == M_LEARNED || (mode == M_FRONTIER && pj == 0)) push[npush++] = x;
     }
@@ -298,21 +339,21 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
             atomicAdd(&P.rc[xc[a]], 1);
         }
     }
-    // net reference changes of matched nodes, positive ones first
+    // net reference changes of matched nodes, positive ones first; fire and
+    // forget (no return value on the critical path): every decrement counts as
+    // a possible death for the collection trigger, collection finds the real
+    // ones
     for (int d = 0; d < ndelta; d++) {
         int32_t w = delta[d];
         int32_t q = w & 0xff, dv = w >> 8;
-        int32_t old = atomicAdd(&P.rc[reg[q]], dv);
-        if (dv < 0 && old + dv == 0) C.deaths++;
+        atomicAdd(&P.rc[reg[q]], dv);
+        if (dv < 0) C.deaths++;
     }
     if (rootvar) {
         P.hs[i] = xh;
         for (int a = 0; a < xa; a++) P.args[a * cap + i] = xc[a];
         P.nfs[i] = (int32_t)(k + 1);
-        if (mode == M_FRONTIER) {
-            int32_t p = P.par[i];
-            if (p != 0 && atomicSub(&P.pend[p], 1) == 1) push[npush++] = p;
-        }
+        if (mode == M_FRONTIER) notify_parent(P, i, push, npush);
     } else {
         P.hs[i] = R[1];
         for (int a = 0; a < root_nargs; a++) {
@@ -355,9 +396,10 @@ __device__ __forceinline__ void flush_counters(Counters &C, Acc *A)
 
 // One decision + allocation + application + push for every lane of a warp
 // (lane-uniform control flow; `cand` marks lanes with a node to consider).
-__device__ __forceinline__ void process_warp(const DevPool &P, const Tab &T, const State &S,
-                                             Acc *A, int mode, bool cand, bool keep, int32_t i,
-                                             bool check_ready, int32_t *next_buf, Counters &C)
+__device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, const State &S,
+                                                Acc *A, int mode, bool cand, bool keep, int32_t i,
+                                                bool check_ready, int32_t *next_buf, Counters &C,
+                                                bool eager = false)
 {
     int32_t reg[TRS_MAX_PATTERN];
     int32_t nw[TRS_MAX_RHS];
@@ -376,8 +418,14 @@ __device__ __forceinline__ void process_warp(const DevPool &P, const Tab &T, con
         if (!warp_alloc(P, S, A, m, nw)) d = D_NONE;
     }
     if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, d, S.k, reg, nw, C, push, npush);
+    // eager continuation: keep one of the nodes that just became ready (the
+    // last pushed: the redex itself, else its parent, else a new node) and
+    // process it at once instead of in the next sweep
+    int32_t cont = -1;
+    if (eager && npush > 0) cont = push[--npush];
     if (mode != M_PLAIN && __any_sync(kFull, npush > 0))
         warp_push(next_buf, &A->pushes, P.cap, npush, push, P.ctl);
+    return cont;
 }
 
 // ---------------------------------------------------------------------------
@@ -418,31 +466,73 @@ __device__ void phase_plain(const DevPool &P, const Tab &T, const State &S, Acc 
     flush_counters(C, A);
 }
 
-// Frontier sweep: visit the entries of the current frontier buffer.
+// Frontier sweep: visit the entries of the current frontier buffer.  With an
+// eager budget, a lane that makes a node ready keeps processing it (up to
+// `eager` nodes per frontier entry), and idle lanes take the next unclaimed
+// entries (one atomic per warp), so chains of dependent rewrites advance many
+// steps per sweep.  Results and counts are those of the synchronous sweep;
+// only the number of sweeps changes.
 __device__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
-                               long long warp0, long long nwarps)
+                               long long warp0, long long nwarps, int eager = 0)
 {
     Counters C{0, 0, 0, 0, 0};
     const int lane = threadIdx.x & 31;
     const int32_t *cur = P.fq[S.cur];
     int32_t *next = P.fq[S.cur ^ 1];
-    const long long nchunks = (S.fsz + 31) / 32;
-    for (long long ch = warp0; ch < nchunks; ch += nwarps) {
-        long long e = ch * 32 + lane;
-        bool cand = false, keep = false;
-        int32_t i = 0;
-        if (e < S.fsz) {
-            i = cur[e];
-            int32_t s = P.nfs[i];
-            // frontier-mode entries are ready by construction; a learned
-            // frontier may hold nodes that are waiting, young or already done
-            if (s < 0) {
-                if (-(long long)s <= S.k) cand = true;
-                else keep = (mode == M_LEARNED);
+    if (eager <= 0 || mode != M_FRONTIER) {
+        const long long nchunks = (S.fsz + 31) / 32;
+        for (long long ch = warp0; ch < nchunks; ch += nwarps) {
+            long long e = ch * 32 + lane;
+            bool cand = false, keep = false;
+            int32_t i = 0;
+            if (e < S.fsz) {
+                i = cur[e];
+                int32_t s = P.nfs[i];
+                // frontier-mode entries are ready by construction; a learned
+                // frontier may hold nodes that are waiting, young or already done
+                if (s < 0) {
+                    if (-(long long)s <= S.k) cand = true;
+                    else keep = (mode == M_LEARNED);
+                }
             }
+            if (!__any_sync(kFull, cand || keep)) continue;
+            process_warp(P, T, S, A, mode, cand, keep, i, mode == M_LEARNED, next, C);
         }
-        if (!__any_sync(kFull, cand || keep)) continue;
-        process_warp(P, T, S, A, mode, cand, keep, i, mode == M_LEARNED, next, C);
+    } else {
+        int32_t node = -1;
+        int steps = 0;
+        bool drained = false;
+        for (;;) {
+            const bool idle = node < 0;
+            const unsigned im = __ballot_sync(kFull, idle);
+            bool fresh_entry = false;
+            if (im && !drained) {
+                const int leader = __ffs(im) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&A->taken, (unsigned long long)__popc(im));
+                base = __shfl_sync(kFull, base, leader);
+                if ((long long)base >= S.fsz) drained = true;
+                if (idle) {
+                    long long e = (long long)base + __popc(im & ((1u << lane) - 1u));
+                    if (e < S.fsz) {
+                        int32_t i = cur[e];
+                        int32_t s = P.nfs[i];
+                        if (s < 0 && -(long long)s <= S.k) { node = i; fresh_entry = true; }
+                    }
+                }
+            }
+            if (fresh_entry) steps = 0;
+            const bool cand = node >= 0;
+            if (!__any_sync(kFull, cand)) {
+                if (drained) break;
+                continue;
+            }
+            int32_t cont = process_warp(P, T, S, A, mode, cand, false, cand ? node : 0, false, next, C, true);
+            steps++;
+            const bool over = cont >= 0 && steps >= eager;
+            if (__any_sync(kFull, over)) warp_push(next, &A->pushes, P.cap, over ? 1 : 0, &cont, P.ctl);
+            node = over ? -1 : cont;
+        }
     }
     flush_counters(C, A);
 }
@@ -564,6 +654,135 @@ __device__ void phase_seed(const DevPool &P, const Tab &T, const State &S, Acc *
             if (threadIdx.x == 0) s_base = atomicAdd(&A->conf_found, (unsigned long long)total);
             __syncthreads();
             if (ready && (long long)s_base + off < P.cap) buf[s_base + off] = (int32_t)i;
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace trs
+
+#include "trs_mlp.cuh"
+
+namespace trs {
+
+// Local view of node i for the predictor: its head, its arguments' heads (0
+// beyond the head's arity) and which arguments are in normal form at sweep k.
+__device__ __forceinline__ void node_features(const DevPool &P, const Tab &T, int32_t i, long long k,
+                                              int &h, int32_t *a, unsigned &bits)
+{
+    h = P.hs[i];
+    const int ar = T.arity(h);
+    bits = 0;
+#pragma unroll
+    for (int j = 0; j < TRS_MAX_ARITY; j++) {
+        a[j] = 0;
+        if (j < P.ma && j < ar) {
+            const int32_t c = P.args[j * P.cap + i];
+            a[j] = P.hs[c];
+            if (is_nf_at(P.nfs[c], k)) bits |= 1u << j;
+        }
+    }
+}
+
+// Learned-frontier refresh: score every live node that is not in normal form
+// with the predictor (BF16 weights in shared memory, FP32 accumulation) and
+// compact those at or above the threshold into the current frontier buffer.
+// Counts all such nodes too: a refresh that finds none is the full sweep that
+// confirms termination.
+__device__ void phase_refresh(const DevPool &P, const Tab &T, const MlpView &M, const State &S, Acc *A,
+                              float thr, long long block0, long long nblocks)
+{
+    __shared__ unsigned long long s_base;
+    int32_t *buf = P.fq[S.cur];
+    const long long n = S.n;
+    const long long per = (long long)blockDim.x;
+    const long long nchunks = (n + per - 1) / per;
+    unsigned long long pend = 0;
+    for (long long ch = block0; ch < nchunks; ch += nblocks) {
+        const long long i = ch * per + threadIdx.x;
+        const bool pending = i >= 1 && i < n && P.nfs[i] < 0;
+        int h = 0;
+        int32_t a[TRS_MAX_ARITY];
+        unsigned bits = 0;
+        if (pending) node_features(P, T, (int32_t)i, S.k, h, a, bits);
+        else {
+#pragma unroll
+            for (int j = 0; j < TRS_MAX_ARITY; j++) a[j] = 0;
+        }
+        const float p = mlp_warp_prob(M, pending, h, a, bits);
+        const bool sel = pending && p >= thr;
+        pend += pending ? 1 : 0;
+        int total = 0;
+        const int off = block_scan_flag(sel, &total);
+        if (total > 0) {
+            if (threadIdx.x == 0) s_base = atomicAdd(&A->refresh_sel, (unsigned long long)total);
+            __syncthreads();
+            if (sel && (long long)s_base + off < P.cap) buf[s_base + off] = (int32_t)i;
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pend += __shfl_down_sync(kFull, pend, o);
+    if ((threadIdx.x & 31) == 0 && pend) atomicAdd(&A->pending, pend);
+}
+
+// Predictor traces, labels: row r was sampled at sweep s; its node acted
+// (was rewritten or marked) before sweep k_until iff act[slot] < k_until.
+__device__ void phase_label(const DevPool &P, long long lo, long long hi, long long k_until)
+{
+    for (long long r = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; r < hi;
+         r += (long long)gridDim.x * blockDim.x)
+        P.samp_label[r] = (long long)P.act[P.samp_slot[r]] < k_until ? 1.f : 0.f;
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    // integer finaliser (xorshift-multiply), used only to pick sample nodes
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// Predictor traces, samples: a hashed subset of the live nodes not in normal
+// form at the start of sweep k; their features become rows and their act[]
+// entries restart.
+__device__ void phase_sample(const DevPool &P, const Tab &T, const State &S, const LaunchOpts &o)
+{
+    __shared__ unsigned long long s_base;
+    const long long n = S.n;
+    const long long per = (long long)blockDim.x;
+    const long long nchunks = (n + per - 1) / per;
+    const int F = 2 + P.ma;
+    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const long long i = ch * per + threadIdx.x;
+        bool take = false;
+        if (i >= 1 && i < n) {
+            const int32_t s = P.nfs[i];
+            if (s < 0 && -(long long)s <= S.k)
+                take = mix32((uint32_t)i * 0x9E3779B1u ^ (uint32_t)S.k * 0x85EBCA77u ^ o.sample_seed) <
+                       o.sample_thresh;
+        }
+        int total = 0;
+        const int off = block_scan_flag(take, &total);
+        if (total > 0) {
+            if (threadIdx.x == 0) s_base = atomicAdd((unsigned long long *)&P.ctl->samp_n, (unsigned long long)total);
+            __syncthreads();
+            const long long r = (long long)s_base + off;
+            if (take && r < P.samp_cap) {
+                int h;
+                int32_t a[TRS_MAX_ARITY];
+                unsigned bits;
+                node_features(P, T, (int32_t)i, S.k, h, a, bits);
+                int32_t *row = P.samp_feat + r * F;
+                row[0] = h;
+                for (int j = 0; j < P.ma; j++) row[1 + j] = a[j];
+                row[1 + P.ma] = (int32_t)bits;
+                P.samp_slot[r] = (int32_t)i;
+                P.act[i] = 0x7fffffff;
+            }
             __syncthreads();
         }
     }

@@ -72,7 +72,9 @@ struct Acc {  // per-sweep accumulators, triple-buffered by sweep number % 3
     unsigned long long pushes;     // entries written to the next frontier
     unsigned long long gc_frees, gc_deaths, gc_append;  // garbage collection
     unsigned long long conf_found, refresh_sel;
-    unsigned long long pad[3];
+    unsigned long long taken;      // eager frontier sweep: entries claimed
+    unsigned long long pending;    // learned refresh: live nodes not in normal form
+    unsigned long long pad[1];
 };
 
 struct Ctl {
@@ -101,6 +103,8 @@ struct Ctl {
     unsigned int solo_gen, pad1;
     long long trace_n;
     long long t_start;      // globaltimer at the start of the current call
+    long long since;        // learned: sweeps since the last refresh
+    long long samp_n;       // predictor traces: rows written
     Acc acc[3];
 };
 
@@ -122,7 +126,14 @@ struct DevPool {
     int32_t ma;
     int32_t tab_words;
     int32_t trace_cap;
+    int32_t nsym;
+    const unsigned char *mlp;  // learned mode: BF16 inference block of the predictor
+    int32_t mlp_bytes;
     int32_t pad;
+    int32_t *samp_feat;        // predictor traces: rows [h, a_0 .. a_{ma-1}, bits]
+    int32_t *samp_slot;
+    float *samp_label;
+    long long samp_cap;
 };
 
 constexpr int kTraceCap = 65536;
@@ -137,9 +148,13 @@ struct LaunchOpts {
     int32_t trace;
     int32_t refresh;
     float threshold;
-    int32_t pad;
+    int32_t eager;
     long long timeout_ns;
     long long time_limit_ns;
+    int32_t sample_period;     // predictor traces: sweeps between samples (0 = off)
+    uint32_t sample_thresh;    // sample a node when its hash is below this
+    uint32_t sample_seed;
+    int32_t pad2;
 };
 
 // compile (host)

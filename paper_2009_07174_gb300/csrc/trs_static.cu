@@ -160,7 +160,7 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
     if (opts) o = *opts;
     else trs_opts_default(&o);
     if (o.mode == TRS_MODE_LEARNED || o.driver != TRS_DRIVER_PERSISTENT || o.block_size < 128 ||
-        o.block_size > 1024 || (o.block_size & (o.block_size - 1)) || o.max_sweeps <= 0 ||
+        o.block_size > 512 || (o.block_size & (o.block_size - 1)) || o.max_sweeps <= 0 ||
         o.timeout_ns <= 0 || o.time_limit_ns <= 0 || o.gc_div <= 0 || o.gc_min_dead < 0 ||
         o.solo_max < 0 || o.grid_blocks < 0)
         return fail("trs_normalize_static: invalid options (plain or frontier mode, persistent driver)",

@@ -192,7 +192,21 @@ def test_solo_episodes(trs, solo):
     check(trs, ti.FIB, terms, modes=["frontier"], solo_max=solo)
 
 
-@pytest.mark.parametrize("block", [128, 256, 1024])
+@pytest.mark.parametrize("eager,solo", [(1, 0), (8, 0), (1024, 0), (1024, 512)])
+def test_eager_continuation(trs, eager, solo):
+    """Eager continuation changes only the number of sweeps: normal forms,
+    rewrites and nf marks are those of the synchronous sweep."""
+    flat, offs, meta = ti.arith_batch(seed=5, count=40, dmin=2, dmax=6)
+    terms = ti.split_terms(flat, offs) + [ti.fib_term(n) for n in (0, 7, 16)]
+    for t, ts in ((ti.ARITH, terms[:40]), (ti.FIB, terms[40:])):
+        check(trs, t, ts, modes=["frontier"], check_sweeps=False, eager=eager, solo_max=solo)
+    term, _ = ti.msort_batch(seed=8, nlists=8, lmin=1, lmax=40, vmax=12)
+    check(trs, ti.MSORT, [term], modes=["frontier"], check_sweeps=False, eager=eager, solo_max=solo)
+    check(trs, ti.TTREE, [ti.ttree_term(7)], modes=["frontier"], check_sweeps=False, eager=eager,
+          solo_max=solo)
+
+
+@pytest.mark.parametrize("block", [128, 256, 512])
 def test_block_sizes(trs, block):
     terms = [ti.fib_term(n) for n in range(5, 12)]
     check(trs, ti.FIB, terms, block_size=block)

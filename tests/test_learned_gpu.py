@@ -1,0 +1,233 @@
+"""Learned frontier (GPU): the predictor's kernels against the float64 oracle
+(oracle/mlp.py), trace collection, and exactness of learned-mode normal forms
+whatever the predictor says."""
+import numpy as np
+import pytest
+
+import trs_inputs as ti
+from oracle import Oracle, mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2009_07174_gb300 as trs
+    return torch, trs
+
+
+def to_bf16(x):
+    """float32 -> bfloat16 (round to nearest even), returned as float32."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+def random_rows(t, n, seed):
+    rng = np.random.default_rng(seed)
+    ma = int(max(t.arity))
+    feat = np.zeros((n, 2 + ma), dtype=np.int32)
+    feat[:, 0] = rng.integers(1, t.nsym, n)
+    for j in range(ma):
+        feat[:, 1 + j] = rng.integers(0, t.nsym, n)
+    feat[:, 1 + ma] = rng.integers(0, 1 << ma, n)
+    y = rng.integers(0, 2, n).astype(np.float32)
+    return feat, y
+
+
+def fill(torch, samples, feat, y):
+    n = len(feat)
+    samples.feat[:n] = torch.from_numpy(feat).cuda()
+    samples.label[:n] = torch.from_numpy(y).cuda()
+    samples.n = n
+
+
+@pytest.mark.parametrize("t", [ti.FIB, ti.MSORT])
+def test_gradient_matches_oracle(env, t):
+    torch, trs = env
+    prog = trs.trs_compile(t)
+    pred = trs.Predictor(prog, seed=3)
+    nsym, ma, H = t.nsym, int(max(t.arity)), 32
+    rng = np.random.default_rng(1)
+    theta = rng.normal(0, 0.4, size=pred.nparams).astype(np.float32)
+    pred.set_params(theta)
+    feat, y = random_rows(t, 3000, 2)
+    s = trs.Samples(prog, 4096)
+    fill(torch, s, feat, y)
+    for pw in (1.0, 2.5):
+        g, loss = pred.grad(s, len(feat), pos_weight=pw)
+        gw = mlp.grad(theta.astype(np.float64), feat, y, nsym, ma, H, pw)
+        lw = mlp.loss(theta.astype(np.float64), feat, y, nsym, ma, H, pw)
+        scale = np.max(np.abs(gw))
+        # FP32 sums of up to 3000 terms in any order: 1e-4 of the largest entry
+        assert np.max(np.abs(g - gw)) <= 1e-4 * scale, np.max(np.abs(g - gw)) / scale
+        assert abs(loss - lw) <= 1e-5 * max(1.0, abs(lw))
+
+
+@pytest.mark.parametrize("t", [ti.FIB, ti.MSORT])
+def test_inference_matches_oracle(env, t):
+    torch, trs = env
+    prog = trs.trs_compile(t)
+    pred = trs.Predictor(prog, seed=4)
+    nsym, ma, H = t.nsym, int(max(t.arity)), 32
+    rng = np.random.default_rng(7)
+    theta = rng.normal(0, 0.5, size=pred.nparams).astype(np.float32)
+    pred.set_params(theta)
+    feat, _ = random_rows(t, 5000, 8)
+    dfeat = torch.from_numpy(feat).cuda()
+    # FP32 logits against the float64 network with the same weights
+    z32 = pred.logits32(dfeat).cpu().numpy()
+    zw, _ = mlp.forward(theta.astype(np.float64), feat, nsym, ma, H)
+    assert np.max(np.abs(z32 - zw)) <= 1e-4 * max(1.0, np.max(np.abs(zw)))
+    # BF16 weights (biases stay FP32), FP32 accumulation: the float64 network
+    # evaluated on the same BF16-rounded weights
+    d, sizes = mlp.dims(nsym, ma, H)
+    tb = theta.astype(np.float64).copy()
+    at = 0
+    for k, sz in enumerate(sizes):
+        if k in (0, 2, 4):
+            tb[at:at + sz] = to_bf16(theta[at:at + sz])
+        at += sz
+    p = pred.infer(dfeat).cpu().numpy()
+    pw = mlp.prob(tb, feat, nsym, ma, H)
+    assert np.max(np.abs(p - pw)) <= 1e-4
+
+
+def test_adam_steps_match_oracle(env):
+    torch, trs = env
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    pred = trs.Predictor(prog, seed=5)
+    nsym, ma, H = t.nsym, 2, 32
+    theta = pred.get_params().astype(np.float64)
+    feat, y = random_rows(t, 2048, 9)
+    s = trs.Samples(prog, 2048)
+    fill(torch, s, feat, y)
+    pred.set_params(theta.astype(np.float32))
+    pred.train(s, 2048, epochs=3, batch=1024, lr=1e-2)
+    got = pred.get_params()
+    th, m, v = theta.copy(), np.zeros_like(theta), np.zeros_like(theta)
+    step = 0
+    for _ in range(3):
+        for lo in range(0, 2048, 1024):
+            step += 1
+            g = mlp.grad(th, feat[lo:lo + 1024], y[lo:lo + 1024], nsym, ma, H)
+            th, m, v = mlp.adam_step(th, g, m, v, step, lr=1e-2)
+    # Adam divides by sqrt(v): entries with tiny gradients amplify FP32 noise;
+    # bound by a fraction of the total movement lr * steps
+    assert np.max(np.abs(got - th)) <= 0.05 * 1e-2 * step
+
+
+def test_collect_samples_and_label_semantics(env):
+    torch, trs = env
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    pool = trs.Pool(prog, 1 << 20)
+    flat, offs = ti.concat_terms([ti.fib_term(n) for n in range(5, 16)])
+    roots = pool.term_upload_batch(flat, offs)
+    s = trs.Samples(prog, 200000)
+    n, st = pool.trs_collect_samples(s, period=8, rate=1.0, mode="frontier")
+    assert n > 1000 and st["status"] == 0
+    # the result is unaffected by sampling
+    o = Oracle(t)
+    got = pool.term_download_batch(roots)
+    for g, term in zip(got, [ti.fib_term(n) for n in range(5, 16)]):
+        assert np.array_equal(g, o.normalize(term).term)
+    feat = s.feat[:n].cpu().numpy()
+    lab = s.label[:n].cpu().numpy()
+    assert set(np.unique(lab)) <= {0.0, 1.0}
+    ar = t.arity[feat[:, 0]]
+    full = (1 << ar) - 1
+    ready = (feat[:, 3] & full) == full
+    # a node whose arguments are all normal forms acts in the very next sweep
+    assert np.all(lab[ready] == 1.0)
+    assert 0 < lab.mean() < 1
+    # arguments beyond the head's arity are encoded as symbol 0
+    assert np.all(feat[ar < 2, 2] == 0) and np.all(feat[ar < 1, 1] == 0)
+
+
+def trained_predictor(torch, trs, prog, t, terms, period=16):
+    pool = trs.Pool(prog, 1 << 22)
+    flat, offs = ti.concat_terms(terms)
+    pool.term_upload_batch(flat, offs)
+    s = trs.Samples(prog, 1 << 20)
+    n, _ = pool.trs_collect_samples(s, period=period, rate=1.0, mode="frontier")
+    pred = trs.Predictor(prog, seed=11)
+    losses = pred.train(s, n, epochs=8, batch=4096, lr=5e-3)
+    assert losses[-1] < losses[0]
+    return pred
+
+
+@pytest.mark.parametrize("thr", [0.0, 0.5, 1.01])
+def test_learned_mode_is_exact(env, thr):
+    """Whatever the predictor selects (everything, its own choice, nothing),
+    learned-mode normal forms and counts equal the oracle's."""
+    torch, trs = env
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    pred = trained_predictor(torch, trs, prog, t, [ti.fib_term(n) for n in range(8, 17)])
+    terms = [ti.fib_term(n) for n in (0, 3, 11, 17)]
+    o = Oracle(t)
+    want = [o.normalize(x) for x in terms]
+    pool = trs.Pool(prog, 1 << 22)
+    pool.trs_pool_attach_predictor(pred)
+    flat, offs = ti.concat_terms(terms)
+    roots = pool.term_upload_batch(flat, offs)
+    st = pool.trs_normalize(mode="learned", threshold=thr, refresh=16)
+    got = pool.term_download_batch(roots)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w.term)
+    assert st["rewrites"] == sum(w.rewrites for w in want)
+    assert st["nf_marks"] == sum(w.nf_marks for w in want)
+    assert st["refreshes"] >= 1
+
+
+def test_learned_mode_other_workloads(env):
+    torch, trs = env
+    for t, terms in ((ti.ARITH, ti.split_terms(*ti.arith_batch(seed=2, count=30, dmin=2, dmax=6)[:2])),
+                     (ti.MSORT, [ti.msort_batch(seed=3, nlists=4, lmin=2, lmax=30, vmax=9)[0]])):
+        prog = trs.trs_compile(t)
+        pred = trained_predictor(torch, trs, prog, t, terms, period=8)
+        o = Oracle(t)
+        want = [o.normalize(x) for x in terms]
+        pool = trs.Pool(prog, 1 << 22)
+        pool.trs_pool_attach_predictor(pred)
+        flat, offs = ti.concat_terms(terms)
+        roots = pool.term_upload_batch(flat, offs)
+        st = pool.trs_normalize(mode="learned", refresh=8, threshold=0.3)
+        for g, w in zip(pool.term_download_batch(roots), want):
+            assert np.array_equal(g, w.term)
+        assert st["rewrites"] == sum(w.rewrites for w in want)
+
+
+def test_learned_without_predictor_is_refused(env):
+    torch, trs = env
+    prog = trs.trs_compile(ti.FIB)
+    pool = trs.Pool(prog, 1024)
+    with pytest.raises(trs.TrsError) as e:
+        pool.trs_normalize(mode="learned")
+    assert e.value.name == "TRS_ERR_NO_PREDICTOR"
+
+
+def test_trained_predictor_visits_fewer_nodes_than_plain(env):
+    """What the trained network gains over the method without it: the plain
+    all-node sweep examines every live node that is not in normal form every
+    sweep; the learned frontier examines far fewer at the same result."""
+    torch, trs = env
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    pred = trained_predictor(torch, trs, prog, t, [ti.fib_term(n) for n in range(8, 18)])
+    res = {}
+    for mode in ("plain", "learned"):
+        pool = trs.Pool(prog, 1 << 22)
+        pool.trs_pool_attach_predictor(pred)
+        r = pool.term_upload(ti.fib_term(19))
+        res[mode] = (pool.trs_normalize(mode=mode, refresh=16, threshold=0.5), pool.term_download(r))
+    assert np.array_equal(res["plain"][1], res["learned"][1])
+    assert res["learned"][0]["rewrites"] == res["plain"][0]["rewrites"]
+    assert res["learned"][0]["visits"] < 0.5 * res["plain"][0]["visits"]
