@@ -5,8 +5,10 @@ Workload: one term fib(S^22(0)) in a node pool of 2^24 slots, normalised to
 S^17711(0) (186,579 rewrites).  A step is one normalisation of that term
 through the C ABI; the term is uploaded before each step's timed region
 (inputs resident in HBM), and L2 is flushed between steps.  The headline
-engine runs next to the plain all-node sweep (the paper's topology-driven
-derive kernel) on the same term.
+engine (exact frontier with eager continuation, autotuned options) runs next
+to the plain all-node sweep (the paper's topology-driven derive kernel) and
+the learned frontier, whose predictor is trained on the engine's own traces
+of smaller Fibonacci terms before anything is timed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 (torchrun, one rank per GPU) every rank normalises its own replica
@@ -140,72 +142,70 @@ def alg_bytes(st, trace, ma):
 def run_ours(args, rank, ws, local):
     import torch
     import paper_2009_07174_gb300 as trs
-    from paper_2009_07174_gb300 import autotune_defaults
+    from paper_2009_07174_gb300 import autotune_defaults, learn
 
     torch.cuda.set_device(local)
     term = ti.fib_term(FIB_N)
     prog = trs.trs_compile(ti.FIB)
     pool = trs.Pool(prog, POOL)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    opts_kw = autotune_defaults(args.mode)
-    mode = opts_kw["mode"]
     stream = torch.cuda.current_stream()
 
-    def one(opts_kw, trace=0):
+    def one(kw, trace=0):
         pool.trs_pool_reset()
         root = pool.term_upload(term)
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        pool.trs_normalize(wait=False, trace=trace, **opts_kw)
+        pool.trs_normalize(wait=False, trace=trace, **kw)
         e1.record(stream)
         return root, e0, e1
 
-    # warm-up (also checks the result once)
-    for _ in range(max(args.warmup, 3)):
-        root, e0, e1 = one(opts_kw)
-    st = pool.trs_pool_stats()
-    res = pool.term_download(root)
-    assert len(res) == 17712 and st["rewrites"] == 186579, st
-
-    barrier()
-    torch.cuda.synchronize()
-    times = []
-    with Clocks(local) as clk:
-        for _ in range(args.steps):
-            root, e0, e1 = one(opts_kw)
+    def timed(kw, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            root, e0, e1 = one(kw)
+        st = pool.trs_pool_stats()
+        res = pool.term_download(root)
+        assert len(res) == 17712 and st["rewrites"] == 186579, st
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            root, e0, e1 = one(kw)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+        return sum(times) / len(times), pool.trs_pool_stats()
+
+    # the predictor of the learned frontier, trained on the engine's own traces
+    # of smaller Fibonacci terms before anything is timed
+    flat, offs = ti.concat_terms([ti.fib_term(n) for n in range(8, 21)])
+    pred, info = learn.train_for(prog, flat, offs, 1 << 24, period=16, return_info=True)
+    pool.trs_pool_attach_predictor(pred)
+
+    head_kw = autotune_defaults(args.mode, "fib22")
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ms, st = timed(head_kw, args.steps, args.warmup)
         torch.cuda.synchronize()
     barrier()
-    ms = sum(times) / len(times)
     ms_max = reduce_max(ms)
-    st = pool.trs_pool_stats()
     rewrites = st["rewrites"]
     value = rewrites * ws / (ms_max / 1e3)
 
     # roofline of the engine kernel (one launch per step) with the per-sweep trace
-    root, e0, e1 = one(opts_kw, trace=1)
+    root, e0, e1 = one(head_kw, trace=1)
     torch.cuda.synchronize()
     tr = pool.trs_trace_read()
     st_tr = pool.trs_pool_stats()
-    st_tr["mode"] = mode
+    st_tr["mode"] = head_kw["mode"]
     nbytes = alg_bytes(st_tr, tr, prog.maxarity)
     peak, peak_kind = peaks()
     achieved = nbytes / (ms / 1e3) / 1e9
 
-    # plain all-node sweep on the same term (the method without the frontier)
-    plain_kw = dict(opts_kw, mode="plain")
-    root, e0, e1 = one(plain_kw)
-    torch.cuda.synchronize()
-    plain_times = []
-    for _ in range(2):
-        root, e0, e1 = one(plain_kw)
-        e1.synchronize()
-        plain_times.append(e0.elapsed_time(e1))
-    plain_ms = sum(plain_times) / len(plain_times)
-    plain_st = pool.trs_pool_stats()
-    assert plain_st["rewrites"] == 186579
+    # the plain all-node sweep (the method without a frontier) and the learned frontier
+    plain_ms, plain_st = timed(autotune_defaults("plain", "fib22"), 2, 1)
+    learned_kw = autotune_defaults("learned", "fib22")
+    learned_ms, learned_st = timed(learned_kw, 3, 1)
 
     # end to end through the C ABI with host buffers: upload, normalise, download
     e2e_times = []
@@ -215,23 +215,26 @@ def run_ours(args, rank, ws, local):
         t0 = time.perf_counter()
         pool.trs_pool_reset()
         r = pool.term_upload(term)
-        pool.trs_normalize(**opts_kw)
+        pool.trs_normalize(**head_kw)
         out = pool.term_download(r)
         t1 = time.perf_counter()
         e2e_times.append(t1 - t0)
         h2d = len(term) * 4 * (4 + prog.maxarity) + 8
         d2h = st["high_water"] * 4 * (1 + prog.maxarity) + 8
         assert len(out) == 17712
-    e2e = rewrites / statistics.mean(e2e_times)
-    e2e = reduce_max(0) if False else e2e
+    e2e = rewrites * ws / reduce_max(statistics.mean(e2e_times))
 
     return {
-        "value": value, "ms": ms_max, "stats": st, "mode": mode, "opts": opts_kw,
+        "value": value, "ms": ms_max, "stats": st, "mode": head_kw["mode"], "opts": head_kw,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": nbytes},
         "plain": {"ms": plain_ms, "value": rewrites / (plain_ms / 1e3),
                   "sweeps": plain_st["sweeps"], "visits": plain_st["visits"]},
+        "learned": {"ms": learned_ms, "value": rewrites / (learned_ms / 1e3), "opts": learned_kw,
+                    "sweeps": learned_st["sweeps"], "visits": learned_st["visits"],
+                    "refreshes": learned_st["refreshes"], "train_rows": info["rows"],
+                    "train_loss": [round(info["losses"][0], 4), round(info["losses"][-1], 4)]},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
         "gpu_launches": 2 * args.steps,
@@ -254,8 +257,48 @@ def cpu_baseline(target_s=10.0):
             "seconds": dt}
 
 
+PROFILE_CASES = {
+    # name: (workload, pool capacity, launch options) -- single normalisations
+    # for profilers (a few GB on the device at most)
+    "fib22-frontier": ("fib22", 1 << 24, None),
+    "fib22-plain": ("fib22", 1 << 24, {"mode": "plain"}),
+    "fib-batch-frontier": ("fib-batch", 1 << 26, None),
+    "fib-batch-plain": ("fib-batch", 1 << 26, {"mode": "plain", "max_sweeps": 64}),
+    "arith-frontier": ("arith", 1 << 26, None),
+    "ttree-frontier": ("ttree", 1 << 24, None),
+}
+
+
+def run_case(name, reps):
+    """One case of PROFILE_CASES, `reps` times (exit status 0 also when a
+    plain case stops at its sweep limit on purpose)."""
+    import torch
+    import paper_2009_07174_gb300 as trs
+    from paper_2009_07174_gb300 import autotune, autotune_defaults
+    wl, cap, kw = PROFILE_CASES[name]
+    t, build, _ = autotune.workloads()[wl]
+    flat, offs = build()
+    prog = trs.trs_compile(t)
+    pool = trs.Pool(prog, cap)
+    kw = kw or autotune_defaults("frontier", wl)
+    for _ in range(reps):
+        pool.trs_pool_reset()
+        pool.term_upload_batch(flat, offs)
+        try:
+            st = pool.trs_normalize(**kw)
+        except trs.TrsError as e:
+            if e.name != "TRS_ERR_SWEEP_LIMIT":
+                raise
+            st = {"status": e.name}
+        torch.cuda.synchronize()
+    print(json.dumps({"case": name, "opts": kw, "stats": st}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small case for a profiler and exit")
+    ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -263,6 +306,9 @@ def main():
     ap.add_argument("--mode", default="frontier")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case, args.reps)
+        return
     args.warmup = max(args.warmup, 3)
     rank, ws, local = dist_init()
 
@@ -298,10 +344,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "mode": r["mode"], "driver": r["opts"].get("driver"),
                    "block_size": r["opts"].get("block_size"), "solo_max": r["opts"].get("solo_max"),
+                   "eager": r["opts"].get("eager"),
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "time_to_nf_ms": r["ms"], "plain_sweep": r["plain"],
+        "time_to_nf_ms": r["ms"], "plain_sweep": r["plain"], "learned_frontier": r["learned"],
         "speedup_vs_plain": r["plain"]["ms"] / r["ms"],
+        "learned_speedup_vs_plain": r["plain"]["ms"] / r["learned"]["ms"],
         "sweeps": st["sweeps"], "rewrites": st["rewrites"],
         "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"],
         "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],

@@ -165,8 +165,10 @@ typedef struct {
     int32_t grid_blocks;     /* 0 = as many as fit (persistent) / 4 per SM (others) */
     int64_t max_sweeps;      /* TRS_ERR_SWEEP_LIMIT after this many sweeps */
     int64_t timeout_ns;      /* limit of any one device spin-wait */
-    int32_t gc_min_dead;     /* collect garbage once this many nodes are dead ... */
-    int32_t gc_div;          /* ... and at least high_water / gc_div of them */
+    int32_t gc_min_dead;     /* collect garbage once this many nodes may be dead ... */
+    int32_t gc_div;          /* ... and at least high_water / gc_div of them (0 = 8
+                                in plain mode, 1 in frontier / learned modes), or
+                                when fewer than capacity / 8 slots remain */
     int32_t solo_max;        /* persistent frontier/learned: frontiers up to this size
                                 run on one block without grid barriers (0 = never) */
     int32_t graph_unroll;    /* graph driver: sweeps per loop-condition check */

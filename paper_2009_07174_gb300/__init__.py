@@ -408,8 +408,8 @@ def trs_normalize_static(program: Program, d_term, d_out, d_out_len, stream=None
     return st.as_dict()
 
 
-def autotune_defaults(mode: str = "frontier") -> dict:
-    """Launch options for `mode`: the autotuner's cached choice for this GPU if
-    one exists (see autotune.py), else built-in defaults."""
+def autotune_defaults(mode: str = "frontier", workload: str = "default") -> dict:
+    """Launch options for `mode`: the autotuner's choice for this GPU and
+    workload if one exists (see autotune.py), else built-in defaults."""
     from . import autotune
-    return autotune.choose(mode)
+    return autotune.choose(mode, workload)

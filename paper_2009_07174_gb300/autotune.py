@@ -1,25 +1,36 @@
-"""Autotuner for the engine's launch options (block size, driver, solo-episode
-threshold, learned-frontier threshold and refresh period).
+"""Autotuner for the engine's launch options: block size, driver, solo-episode
+size, eager budget, and the learned frontier's threshold and refresh period.
 
-`tune()` times short normalisations of a representative workload for each
-candidate and stores the fastest per GPU name in a JSON cache
-(`_build/autotune.json` unless TRS_AUTOTUNE_CACHE is set); `choose()` returns
-the cached choice, or defaults when nothing was tuned on this GPU.
+`tune()` times short normalisations of a representative workload for every
+candidate option set (CUDA events, best of `reps`, after one warm-up) and
+stores the fastest per GPU name, workload and mode in a JSON cache;
+`choose()` returns the cached choice, else the tuned values shipped for this
+GPU (`tuned_defaults.json` next to this file), else built-in defaults.
 """
 from __future__ import annotations
 
+import itertools
 import json
 import os
 
-CACHE = os.environ.get("TRS_AUTOTUNE_CACHE",
-                       os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
-                                    "autotune.json"))
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.environ.get("TRS_AUTOTUNE_CACHE", os.path.join(HERE, "_build", "autotune.json"))
+SHIPPED = os.path.join(HERE, "tuned_defaults.json")
 
 DEFAULTS = {
     "plain": {"mode": "plain", "driver": "persistent", "block_size": 512},
-    "frontier": {"mode": "frontier", "driver": "persistent", "block_size": 512, "solo_max": 512},
+    "frontier": {"mode": "frontier", "driver": "persistent", "block_size": 512, "solo_max": 512,
+                 "eager": 64},
     "learned": {"mode": "learned", "driver": "persistent", "block_size": 512, "solo_max": 512,
-                "refresh": 64, "threshold": 0.5},
+                "refresh": 16, "threshold": 0.5},
+}
+
+SPACE = {
+    "plain": {"block_size": [128, 256, 512], "driver": ["persistent", "graph"]},
+    "frontier": {"block_size": [256, 512], "solo_max": [0, 512], "eager": [0, 16, 64, 256],
+                 "driver": ["persistent", "graph"]},
+    "learned": {"block_size": [256, 512], "solo_max": [0, 512], "refresh": [8, 16, 64],
+                "threshold": [0.2, 0.5, 0.8]},
 }
 
 
@@ -36,7 +47,8 @@ def gpu_name() -> str:
 def load_cache(path: str = CACHE) -> dict:
     if os.path.exists(path):
         try:
-            return json.load(open(path))
+            with open(path) as f:
+                return json.load(f)
         except (OSError, ValueError):
             return {}
     return {}
@@ -50,10 +62,127 @@ def save_cache(cache: dict, path: str = CACHE) -> None:
     os.replace(tmp, path)
 
 
-def choose(mode: str, gpu: str | None = None, path: str = CACHE) -> dict:
+def lookup(cache: dict, gpu: str, workload: str, mode: str):
+    return cache.get(gpu, {}).get(workload, {}).get(mode)
+
+
+def choose(mode: str, workload: str = "default", gpu: str | None = None, path: str = CACHE) -> dict:
+    """Launch options for `mode` on `workload`: tuned on this GPU if possible."""
     gpu = gpu or gpu_name()
-    entry = load_cache(path).get(gpu, {}).get(mode)
     out = dict(DEFAULTS[mode])
-    if entry:
-        out.update(entry["opts"])
+    for src in (load_cache(SHIPPED), load_cache(path)):
+        e = lookup(src, gpu, workload, mode) or lookup(src, gpu, "default", mode)
+        if e:
+            out.update(e["opts"])
     return out
+
+
+def candidates(mode: str, space: dict | None = None):
+    """Every option set of the search space (drivers that do not apply to a
+    combination are pruned: solo episodes and eager budgets are frontier
+    features of the persistent and graph drivers alike)."""
+    sp = space or SPACE[mode]
+    keys = sorted(sp)
+    for vals in itertools.product(*(sp[k] for k in keys)):
+        o = dict(DEFAULTS[mode])
+        o.update(dict(zip(keys, vals)))
+        if o.get("driver") == "graph" and o.get("solo_max", 0):
+            continue
+        yield o
+
+
+def tune(mode: str, make_pool, workload: str, reps: int = 2, space: dict | None = None,
+         path: str = CACHE, verbose: bool = False) -> dict:
+    """Time every candidate on pools from `make_pool()` (a fresh pool with the
+    workload uploaded, returning (pool, expected_rewrites)); keep the fastest
+    whose rewrite count is right.  Returns {"opts", "ms", "tried"}."""
+    import torch
+    best = None
+    tried = 0
+    for o in candidates(mode, space):
+        times = []
+        ok = True
+        for r in range(reps + 1):
+            pool, expect = make_pool()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pool.trs_normalize(wait=False, **o)
+            e1.record()
+            e1.synchronize()
+            st = pool.trs_pool_stats()
+            if st["rewrites"] != expect:
+                ok = False
+                break
+            if r > 0:
+                times.append(e0.elapsed_time(e1))
+            del pool
+        tried += 1
+        if not ok:
+            continue
+        ms = min(times)
+        if verbose:
+            print(f"autotune {workload} {mode} {o} {ms:.3f} ms", flush=True)
+        if best is None or ms < best["ms"]:
+            best = {"opts": o, "ms": ms}
+    if best is None:
+        raise RuntimeError("autotune: no candidate produced the expected result")
+    best["tried"] = tried
+    cache = load_cache(path)
+    cache.setdefault(gpu_name(), {}).setdefault(workload, {})[mode] = best
+    save_cache(cache, path)
+    return best
+
+
+def workloads():
+    """Representative (smaller) versions of the benchmark workloads used for
+    tuning: name -> (trs, builder returning (flat, offsets), pool capacity)."""
+    import trs_inputs as ti
+    return {
+        "fib22": (ti.FIB, lambda: ti.concat_terms([ti.fib_term(22)]), 1 << 24),
+        "fib-batch": (ti.FIB, lambda: ti.fib_batch(0, 2000)[:2], 1 << 26),
+        "arith": (ti.ARITH, lambda: ti.arith_batch(0, 128, 10, 12)[:2], 1 << 26),
+        "msort": (ti.MSORT, lambda: ti.concat_terms([ti.msort_batch(0, 16, 64, 256)[0]]), 1 << 24),
+        "ttree": (ti.TTREE, lambda: ti.concat_terms([ti.ttree_term(20)]), 1 << 23),
+    }
+
+
+def main(argv=None):
+    import argparse
+
+    import paper_2009_07174_gb300 as trs
+    from . import learn
+
+    ap = argparse.ArgumentParser(description="tune launch options on this GPU")
+    ap.add_argument("--workloads", default="fib22,fib-batch,arith,msort")
+    ap.add_argument("--modes", default="frontier,learned")
+    ap.add_argument("--out", default=CACHE)
+    ap.add_argument("-v", action="store_true")
+    a = ap.parse_args(argv)
+    W = workloads()
+    for name in a.workloads.split(","):
+        t, build, cap = W[name]
+        flat, offs = build()
+        prog = trs.trs_compile(t)
+        probe = trs.Pool(prog, cap)
+        probe.term_upload_batch(flat, offs)
+        expect = probe.trs_normalize(mode="frontier", eager=64)["rewrites"]
+        del probe
+        pred = None
+        for mode in a.modes.split(","):
+            if mode == "learned":
+                pred = learn.train_for(prog, flat, offs, cap)
+
+            def make_pool():
+                p = trs.Pool(prog, cap)
+                if pred is not None:
+                    p.trs_pool_attach_predictor(pred)
+                p.term_upload_batch(flat, offs)
+                return p, expect
+
+            best = tune(mode, make_pool, name, path=a.out, verbose=a.v)
+            print(json.dumps({"workload": name, "mode": mode, **best}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -13,13 +13,13 @@
 namespace trs {
 // trs_kernels.cu
 size_t engine_smem_bytes(const DevPool &P);
-cudaError_t engine_configure(int block, size_t smem, int *blocks_per_sm);
+cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm);
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
                           unsigned long long cond, cudaStream_t stream);
 cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream);
 cudaError_t reset_launch(const DevPool &P, cudaStream_t stream);
 cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
-void *engine_kernel_ptr();
+void *engine_kernel_ptr(int mode);
 const unsigned char *predictor_block(const trs_predictor *p);
 size_t predictor_block_bytes(const trs_predictor *p);
 const trs_program *predictor_program(const trs_predictor *p);
@@ -131,7 +131,7 @@ void trs_opts_default(trs_opts *o)
     o->max_sweeps = 1LL << 40;
     o->timeout_ns = 10LL * 1000 * 1000 * 1000;
     o->gc_min_dead = 4096;
-    o->gc_div = 8;
+    o->gc_div = 0;
     o->solo_max = 0;
     o->graph_unroll = 16;
     o->refresh = 64;
@@ -299,7 +299,7 @@ static int validate_opts(const trs_opts *o)
 {
     if (o->mode < 0 || o->mode > 2 || o->driver < 0 || o->driver > 2) return TRS_ERR_ARG;
     if (o->block_size != 128 && o->block_size != 256 && o->block_size != 512) return TRS_ERR_ARG;
-    if (o->max_sweeps <= 0 || o->timeout_ns <= 0 || o->gc_div <= 0 || o->gc_min_dead < 0 ||
+    if (o->max_sweeps <= 0 || o->timeout_ns <= 0 || o->gc_div < 0 || o->gc_min_dead < 0 ||
         o->grid_blocks < 0 || o->solo_max < 0 || o->graph_unroll <= 0 || o->time_limit_ns <= 0 ||
         o->eager < 0)
         return TRS_ERR_ARG;
@@ -338,7 +338,7 @@ static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, l
     unsigned long long cond = (unsigned long long)handle;
     void *kargs[4] = {&P, &lo, &bud, &cond};
     cudaKernelNodeParams kp = {};
-    kp.func = engine_kernel_ptr();
+    kp.func = engine_kernel_ptr(o.mode);
     kp.gridDim = dim3((unsigned)o.grid);
     kp.blockDim = dim3((unsigned)o.block);
     kp.sharedMemBytes = (unsigned)engine_smem_bytes(dp);
@@ -374,7 +374,7 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
     }
     const size_t smem = engine_smem_bytes(d);
     int bps = 0;
-    CK(engine_configure(o.block_size, smem, &bps), "occupancy");
+    CK(engine_configure(o.mode, o.block_size, smem, &bps), "occupancy");
     if (bps <= 0) { set_error("trs_normalize: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
     int max_grid = bps * pool->num_sms;
     int grid = o.grid_blocks > 0 ? std::min(o.grid_blocks, max_grid) : max_grid;
@@ -453,7 +453,7 @@ int trs_collect_samples(trs_pool *pool, const trs_opts *opts, int32_t period, fl
     d.samp_label = (float *)((char *)dev_samples + feat_b + ((size_t)cap * 4 + 255) / 256 * 256);
     d.samp_cap = cap;
     int bps = 0;
-    CK(engine_configure(o.block_size, engine_smem_bytes(d), &bps), "occupancy");
+    CK(engine_configure(o.mode, o.block_size, engine_smem_bytes(d), &bps), "occupancy");
     if (bps <= 0) { set_error("trs_collect_samples: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
     LaunchOpts lo{};
     lo.mode = o.mode;

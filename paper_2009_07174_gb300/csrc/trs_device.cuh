@@ -267,6 +267,14 @@ __device__ __forceinline__ void notify_parent(const DevPool &P, int32_t i, int32
     if (pv < 0 || atom_acqrel_add_s32(&P.pend[p], -1) == 1) push[npush++] = p;
 }
 
+// Learned frontier: every node enters the next frontier at most once per
+// sweep; pend[] holds the number of the sweep it was last queued for.
+__device__ __forceinline__ void learned_push(const DevPool &P, int32_t x, long long k_next, int32_t *push,
+                                             int &npush)
+{
+    if (atomicExch(&P.pend[x], (int32_t)k_next) != (int32_t)k_next) push[npush++] = x;
+}
+
 __device__ __forceinline__ int32_t par_word(const Tab &T, int32_t parent, int32_t parent_sym)
 {
     return parent | (T.arity(parent_sym) == 1 ? (int32_t)0x80000000 : 0);
@@ -295,6 +303,10 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
         C.nf_marks++;
         if (mode == M_FRONTIER) notify_parent(P, i, push, npush);
+        if (mode == M_LEARNED) {
+            const int32_t p = P.par[i] & 0x7fffffff;   // the parent may be ready now
+            if (p != 0) learned_push(P, p, k + 1, push, npush);
+        }
         if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
         return;
     }
@@ -324,8 +336,13 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         P.rc[x] = 1;
         P.nfs[x] = stamp_new;
         P.par[x] = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
-        P.pend[x] = pj;
-        if (mode == M_LEARNED || (mode == M_FRONTIER && pj == 0)) push[npush++] = x;
+        if (mode == M_LEARNED) {
+            P.pend[x] = (int32_t)(k + 1);
+            push[npush++] = x;
+        } else {
+            P.pend[x] = pj;
+            if (mode == M_FRONTIER && pj == 0) push[npush++] = x;
+        }
     }
     // root that is a variable x: i becomes a copy of x (x is in normal form)
     int32_t xh = 0, xa = 0;
@@ -354,14 +371,22 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         for (int a = 0; a < xa; a++) P.args[a * cap + i] = xc[a];
         P.nfs[i] = (int32_t)(k + 1);
         if (mode == M_FRONTIER) notify_parent(P, i, push, npush);
+        if (mode == M_LEARNED) {
+            const int32_t p = P.par[i] & 0x7fffffff;
+            if (p != 0) learned_push(P, p, k + 1, push, npush);
+        }
     } else {
         P.hs[i] = R[1];
         for (int a = 0; a < root_nargs; a++) {
             int32_t op = build[a];
             P.args[a * cap + i] = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
         }
-        P.pend[i] = root_pend;
-        if (mode == M_LEARNED || (mode == M_FRONTIER && root_pend == 0)) push[npush++] = i;
+        if (mode == M_LEARNED) {
+            learned_push(P, i, k + 1, push, npush);
+        } else {
+            P.pend[i] = root_pend;
+            if (mode == M_FRONTIER && root_pend == 0) push[npush++] = i;
+        }
     }
     if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
     C.rewrites++;
@@ -407,11 +432,11 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     int npush = 0;
     int d = D_NONE;
     int32_t h = 0;
-    if (keep) push[npush++] = i;  // learned frontier: not yet eligible, keep it
+    if (keep) learned_push(P, i, S.k + 1, push, npush);  // learned: not yet eligible, keep it
     if (cand) {
         C.visits++;
         d = decide(P, T, i, S.k, check_ready, reg, h);
-        if (mode == M_LEARNED && d == D_SKIP) push[npush++] = i;  // still waiting: keep it
+        if (mode == M_LEARNED && d == D_SKIP) learned_push(P, i, S.k + 1, push, npush);  // still waiting
     }
     int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;
     if (__any_sync(kFull, m > 0)) {
@@ -434,7 +459,7 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
 // Plain sweep: visit every slot below the high-water mark (Sec. 3, derive
 // kernel launched for all n terms).  The stamp array is read as int4 (four
 // slots per lane per load, 512 contiguous bytes per warp).
-__device__ void phase_plain(const DevPool &P, const Tab &T, const State &S, Acc *A,
+__device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, const State &S, Acc *A,
                             long long warp0, long long nwarps)
 {
     Counters C{0, 0, 0, 0, 0};
@@ -472,7 +497,7 @@ __device__ void phase_plain(const DevPool &P, const Tab &T, const State &S, Acc 
 // entries (one atomic per warp), so chains of dependent rewrites advance many
 // steps per sweep.  Results and counts are those of the synchronous sweep;
 // only the number of sweeps changes.
-__device__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
+__device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
                                long long warp0, long long nwarps, int eager = 0)
 {
     Counters C{0, 0, 0, 0, 0};
@@ -502,7 +527,18 @@ __device__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, A
         int32_t node = -1;
         int steps = 0;
         bool drained = false;
+        // stop following chains once this sweep's fresh allocations use half
+        // of the slots still above the high-water mark: collection only runs
+        // between sweeps
+        const unsigned long long fresh_budget = (unsigned long long)((P.cap - S.n) / 2);
+        bool pressure = false;
+        int iter = 0;
         for (;;) {
+            if ((++iter & 7) == 0 && !pressure) {
+                unsigned long long f = 0;
+                if (lane == 0) f = *(volatile unsigned long long *)&A->fresh;
+                pressure = __shfl_sync(kFull, f, 0) > fresh_budget;
+            }
             const bool idle = node < 0;
             const unsigned im = __ballot_sync(kFull, idle);
             bool fresh_entry = false;
@@ -529,7 +565,7 @@ __device__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, A
             }
             int32_t cont = process_warp(P, T, S, A, mode, cand, false, cand ? node : 0, false, next, C, true);
             steps++;
-            const bool over = cont >= 0 && steps >= eager;
+            const bool over = cont >= 0 && (steps >= eager || pressure);
             if (__any_sync(kFull, over)) warp_push(next, &A->pushes, P.cap, over ? 1 : 0, &cont, P.ctl);
             node = over ? -1 : cont;
         }
@@ -537,16 +573,22 @@ __device__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, A
     flush_counters(C, A);
 }
 
-// Block-wide exclusive scan of one flag per thread; returns the offset of this
-// thread and writes the block total to *total.  Block size <= 1024.
-__device__ __forceinline__ int block_scan_flag(bool f, int *total)
+// Block-wide exclusive scan of a count per thread (warp shuffles, then one
+// warp scans the warp totals); returns this thread's offset and writes the
+// block total to *total.  Block size <= 1024.
+__device__ __forceinline__ int block_scan_count(int v, int *total)
 {
     __shared__ int s_w[32];
     __shared__ int s_tot;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    unsigned b = __ballot_sync(kFull, f);
-    int in_warp = __popc(b & ((1u << lane) - 1u));
-    if (lane == 0) s_w[wid] = __popc(b);
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    int in_warp = x - v;
+    if (lane == 31) s_w[wid] = x;
     __syncthreads();
     if (wid == 0) {
         int v = lane < nw ? s_w[lane] : 0;
@@ -566,47 +608,80 @@ __device__ __forceinline__ int block_scan_flag(bool f, int *total)
     return off;
 }
 
+// Block-wide exclusive scan of one flag per thread (warp ballot + block scan).
+__device__ __forceinline__ int block_scan_flag(bool f, int *total)
+{
+    return block_scan_count(f ? 1 : 0, total);
+}
+
 // Garbage collection (Sec. 3, collect_free_indices): every slot whose reference
-// count is 0 and that is not already free releases its arguments and is
-// appended to the free ring.  Appends are compacted with a warp ballot and a
-// block scan, one atomic per block and chunk.  Counts that reach 0 here are
-// reclaimed by a later collection unless the slot's own thread sees them in
-// this pass.
-__device__ void phase_gc(const DevPool &P, const Tab &T, const State &S, Acc *A,
-                         long long block0, long long nblocks)
+// count is 0 and that is not already free releases its arguments and joins
+// the free ring.  A slot is claimed by swapping its stamp to 0, so the thread
+// that scans it and a thread that just dropped its count to 0 cannot both free
+// it; the latter follows the chain of nodes it kills (up to kGcWalk per slot),
+// so dropped subterms are reclaimed in one pass.  Appends to the ring are
+// compacted with a block scan, one atomic per block and chunk.
+constexpr int kGcWalk = 24;
+constexpr int kGcPer = 4;  // slots per thread per chunk (one int4 of stamps)
+
+__device__ __forceinline__ void phase_gc(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                                         long long block0, long long nblocks)
 {
     __shared__ unsigned long long s_base;
-    unsigned long long frees = 0, deaths = 0;
+    unsigned long long frees = 0, left = 0;
     const long long n = S.n;
-    const long long per = (long long)blockDim.x;
+    const long long per = (long long)blockDim.x * kGcPer;
     const long long nchunks = (n + per - 1) / per;
     for (long long ch = block0; ch < nchunks; ch += nblocks) {
-        long long i = ch * per + threadIdx.x;
-        bool dead = false;
-        if (i >= 1 && i < n) {
-            int32_t s = P.nfs[i];
-            if (s != 0 && P.rc[i] == 0) dead = true;
+        const long long base = ch * per + (long long)threadIdx.x * kGcPer;
+        int32_t sv[kGcPer] = {0, 0, 0, 0};
+        if (base + kGcPer <= n) {
+            const int4 s4 = *reinterpret_cast<const int4 *>(P.nfs + base);
+            sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
+        } else {
+            for (int t = 0; t < kGcPer; t++)
+                if (base + t < n) sv[t] = P.nfs[base + t];
         }
-        if (dead) {
-            int32_t h = P.hs[i];
-            int ar = T.arity(h);
-            for (int a = 0; a < ar; a++) {
-                int32_t c = P.args[a * P.cap + i];
-                if (atomicSub(&P.rc[c], 1) == 1) deaths++;
+        int32_t freed[kGcWalk];
+        int nfreed = 0;
+        for (int t = 0; t < kGcPer; t++) {
+            const long long i = base + t;
+            if (i < 1 || sv[t] == 0 || P.rc[i] != 0) continue;
+            if (atomicExch(&P.nfs[i], 0) == 0) continue;
+            // claimed: free it and follow the nodes it kills, keeping room for
+            // this thread's remaining slots
+            int32_t stk[kGcWalk];
+            int sp = 0;
+            stk[sp++] = (int32_t)i;
+            const int room = kGcWalk - (kGcPer - 1 - t);
+            while (sp > 0) {
+                const int32_t x = stk[--sp];
+                freed[nfreed++] = x;
+                const int ar = T.arity(P.hs[x]);
+                for (int a = 0; a < ar; a++) {
+                    const int32_t c = P.args[a * P.cap + x];
+                    if (atomicSub(&P.rc[c], 1) == 1) {
+                        if (nfreed + sp < room) {
+                            if (atomicExch(&P.nfs[c], 0) != 0) stk[sp++] = c;
+                        } else {
+                            left++;  // dead, reclaimed by a later pass
+                        }
+                    }
+                }
             }
-            P.nfs[i] = 0;
-            frees++;
         }
+        frees += nfreed;
         int total = 0;
-        int off = block_scan_flag(dead, &total);
+        const int off = block_scan_count(nfreed, &total);
         if (total > 0) {
             if (threadIdx.x == 0) s_base = atomicAdd(&A->gc_append, (unsigned long long)total);
             __syncthreads();
-            if (dead) P.ring[(S.fe + (long long)s_base + off) % P.cap] = (int32_t)i;
+            for (int j = 0; j < nfreed; j++)
+                P.ring[(S.fe + (long long)s_base + off + j) % P.cap] = freed[j];
             __syncthreads();
         }
     }
-    unsigned long long x = frees, y = deaths;
+    unsigned long long x = frees, y = left;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         x += __shfl_down_sync(kFull, x, o);
@@ -623,37 +698,45 @@ __device__ void phase_gc(const DevPool &P, const Tab &T, const State &S, Acc *A,
 // nodes with none to the current frontier buffer.  Run at the start of a
 // normalisation and, as the full confirmation sweep, whenever the frontier
 // becomes empty.
-__device__ void phase_seed(const DevPool &P, const Tab &T, const State &S, Acc *A,
-                           long long block0, long long nblocks)
+__device__ __forceinline__ void phase_seed(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                                           long long block0, long long nblocks)
 {
     __shared__ unsigned long long s_base;
     int32_t *buf = P.fq[S.cur];
     const long long n = S.n;
-    const long long per = (long long)blockDim.x;
+    const long long per = (long long)blockDim.x * 4;
     const long long nchunks = (n + per - 1) / per;
     for (long long ch = block0; ch < nchunks; ch += nblocks) {
-        long long i = ch * per + threadIdx.x;
-        bool ready = false;
-        if (i >= 1 && i < n) {
-            int32_t s = P.nfs[i];
-            if (s < 0) {
-                int32_t h = P.hs[i];
-                int ar = T.arity(h);
-                int cnt = 0;
-                for (int a = 0; a < ar; a++) {
-                    int32_t c = P.args[a * P.cap + i];
-                    if (!is_nf_at(P.nfs[c], S.k)) cnt++;
-                }
-                P.pend[i] = cnt;
-                ready = (cnt == 0) && (-(long long)s <= S.k);
+        const long long base = ch * per + (long long)threadIdx.x * 4;
+        int32_t sv[4] = {0, 0, 0, 0};
+        if (base + 4 <= n) {
+            const int4 s4 = *reinterpret_cast<const int4 *>(P.nfs + base);
+            sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
+        } else {
+            for (int t = 0; t < 4; t++)
+                if (base + t < n) sv[t] = P.nfs[base + t];
+        }
+        int32_t ready[4];
+        int nready = 0;
+        for (int t = 0; t < 4; t++) {
+            const long long i = base + t;
+            if (i < 1 || sv[t] >= 0) continue;
+            const int ar = T.arity(P.hs[i]);
+            int cnt = 0;
+            for (int a = 0; a < ar; a++) {
+                const int32_t c = P.args[a * P.cap + i];
+                if (!is_nf_at(P.nfs[c], S.k)) cnt++;
             }
+            P.pend[i] = cnt;
+            if (cnt == 0 && -(long long)sv[t] <= S.k) ready[nready++] = (int32_t)i;
         }
         int total = 0;
-        int off = block_scan_flag(ready, &total);
+        const int off = block_scan_count(nready, &total);
         if (total > 0) {
             if (threadIdx.x == 0) s_base = atomicAdd(&A->conf_found, (unsigned long long)total);
             __syncthreads();
-            if (ready && (long long)s_base + off < P.cap) buf[s_base + off] = (int32_t)i;
+            for (int j = 0; j < nready; j++)
+                if ((long long)s_base + off + j < P.cap) buf[s_base + off + j] = ready[j];
             __syncthreads();
         }
     }
@@ -689,7 +772,7 @@ __device__ __forceinline__ void node_features(const DevPool &P, const Tab &T, in
 // compact those at or above the threshold into the current frontier buffer.
 // Counts all such nodes too: a refresh that finds none is the full sweep that
 // confirms termination.
-__device__ void phase_refresh(const DevPool &P, const Tab &T, const MlpView &M, const State &S, Acc *A,
+__device__ __forceinline__ void phase_refresh(const DevPool &P, const Tab &T, const MlpView &M, const State &S, Acc *A,
                               float thr, long long block0, long long nblocks)
 {
     __shared__ unsigned long long s_base;
@@ -728,7 +811,7 @@ __device__ void phase_refresh(const DevPool &P, const Tab &T, const MlpView &M, 
 
 // Predictor traces, labels: row r was sampled at sweep s; its node acted
 // (was rewritten or marked) before sweep k_until iff act[slot] < k_until.
-__device__ void phase_label(const DevPool &P, long long lo, long long hi, long long k_until)
+__device__ __forceinline__ void phase_label(const DevPool &P, long long lo, long long hi, long long k_until)
 {
     for (long long r = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; r < hi;
          r += (long long)gridDim.x * blockDim.x)
@@ -749,7 +832,7 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x)
 // Predictor traces, samples: a hashed subset of the live nodes not in normal
 // form at the start of sweep k; their features become rows and their act[]
 // entries restart.
-__device__ void phase_sample(const DevPool &P, const Tab &T, const State &S, const LaunchOpts &o)
+__device__ __forceinline__ void phase_sample(const DevPool &P, const Tab &T, const State &S, const LaunchOpts &o)
 {
     __shared__ unsigned long long s_base;
     const long long n = S.n;

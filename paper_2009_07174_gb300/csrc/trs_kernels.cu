@@ -116,10 +116,17 @@ __device__ Flags end_sweep(State &S, const AccVals &V, const LaunchOpts &o, long
         S.since += 1;
         F.refresh = S.fsz == 0 || !action || S.since >= o.refresh;
     }
+    // collection trigger: the plain sweep scans every slot below the high-water
+    // mark, so it collects early (dead >= n / 8 by default) to keep the mark
+    // low; the frontier modes only pay for collection, so they collect when
+    // the dead estimate reaches the high-water mark itself (by default) or
+    // when fewer than cap / 8 slots remain free (above the mark or in the ring)
+    const int div = o.gc_div > 0 ? o.gc_div : (o.mode == M_PLAIN ? 8 : 1);
     long long thr = (long long)o.gc_min_dead;
-    long long frac = S.n / (o.gc_div > 0 ? o.gc_div : 8);
+    const long long frac = S.n / div;
     if (frac > thr) thr = frac;
-    if (S.dead > 0 && (S.dead >= thr || S.n > cap - cap / 16)) F.gc = true;
+    const long long free_slots = (cap - S.n) + (S.fe - S.fb);
+    if (S.dead > 0 && (S.dead >= thr || free_slots < cap / 8)) F.gc = true;
     if (S.left <= 0 && !F.confirm && !F.refresh) F.stop = true;
     return F;
 }
@@ -152,9 +159,14 @@ __device__ __forceinline__ void note_sweep(LocalStats &L, const AccVals &V, cons
     if (now_ns() - ctl->t_start > o.time_limit_ns) atomicCAS(&ctl->status, 0, TRS_ERR_TIMEOUT);
 }
 
-__global__ void __launch_bounds__(512)
-k_engine(DevPool P, LaunchOpts o, long long budget, unsigned long long cond)
+// One instantiation per mode: the plain sweep needs few registers and gains
+// from two resident blocks per SM; the frontier and learned paths get 128.
+template <int MODE>
+__global__ void __launch_bounds__(512, MODE == M_PLAIN ? 2 : 1)
+k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
 {
+    LaunchOpts o = o_in;
+    o.mode = MODE;
     extern __shared__ int32_t smem[];
     __shared__ Acc s_acc;
     __shared__ int s_flag;
@@ -405,17 +417,24 @@ __global__ void k_reset(DevPool P)
 // ---------------------------------------------------------------------------
 // host-side launch helpers (called from trs_api.cu)
 
+static void *engine_fn(int mode)
+{
+    if (mode == M_PLAIN) return (void *)k_engine<M_PLAIN>;
+    if (mode == M_FRONTIER) return (void *)k_engine<M_FRONTIER>;
+    return (void *)k_engine<M_LEARNED>;
+}
+
 size_t engine_smem_bytes(const DevPool &P)
 {
     return mlp_up16((size_t)P.tab_words * sizeof(int32_t)) + (P.mlp ? (size_t)P.mlp_bytes : 0);
 }
 
-cudaError_t engine_configure(int block, size_t smem, int *blocks_per_sm)
+cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const void *fn = engine_fn(mode);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_engine, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
@@ -431,7 +450,12 @@ cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budge
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_engine, P, o, budget, cond);
+    DevPool p = P;
+    LaunchOpts oo = o;
+    long long b = budget;
+    unsigned long long c = cond;
+    void *args[4] = {&p, &oo, &b, &c};
+    return cudaLaunchKernelExC(&cfg, engine_fn(o.mode), args);
 }
 
 cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream)
@@ -479,6 +503,6 @@ cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t s
     return cudaGetLastError();
 }
 
-void *engine_kernel_ptr() { return (void *)k_engine; }
+void *engine_kernel_ptr(int mode) { return engine_fn(mode); }
 
 }  // namespace trs

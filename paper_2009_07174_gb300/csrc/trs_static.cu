@@ -24,7 +24,7 @@
 
 namespace trs {
 size_t engine_smem_bytes(const DevPool &P);
-cudaError_t engine_configure(int block, size_t smem, int *blocks_per_sm);
+cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm);
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
                           unsigned long long cond, cudaStream_t stream);
 cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
@@ -161,7 +161,7 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
     else trs_opts_default(&o);
     if (o.mode == TRS_MODE_LEARNED || o.driver != TRS_DRIVER_PERSISTENT || o.block_size < 128 ||
         o.block_size > 512 || (o.block_size & (o.block_size - 1)) || o.max_sweeps <= 0 ||
-        o.timeout_ns <= 0 || o.time_limit_ns <= 0 || o.gc_div <= 0 || o.gc_min_dead < 0 ||
+        o.timeout_ns <= 0 || o.time_limit_ns <= 0 || o.gc_div < 0 || o.gc_min_dead < 0 ||
         o.solo_max < 0 || o.grid_blocks < 0)
         return fail("trs_normalize_static: invalid options (plain or frontier mode, persistent driver)",
                     TRS_ERR_ARG);
@@ -193,7 +193,7 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
                     std::to_string(cap - 1) + "-slot static node store", TRS_ERR_TOO_BIG);
     int sms = 0, bps = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = engine_configure(o.block_size, engine_smem_bytes(d), &bps);
+    if (e == cudaSuccess) e = engine_configure(o.mode, o.block_size, engine_smem_bytes(d), &bps);
     if (e != cudaSuccess || bps <= 0) return fail("trs_normalize_static: occupancy query failed", TRS_ERR_CUDA);
     LaunchOpts lo{};
     lo.mode = o.mode;
