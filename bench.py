@@ -119,6 +119,39 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def kernel_source_hash():
+    """SHA-256 over the engine's CUDA sources: identifies the kernel version an
+    ncu capture was taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2009_07174_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch recorded in profiles/<name>.md by an ncu capture
+    (dram__bytes_read.sum + dram__bytes_write.sum), or None when the kernel
+    sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split("=", 1)
+            vals[k.strip().strip("`")] = v.strip().strip("`")
+    if vals.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return int(float(vals["traffic_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
 def alg_bytes(st, trace, ma):
     """Algorithmic bytes of one normalisation (the byte model of the design
     notes): the all-slot stamp scans, the per-node reads of visited nodes and
@@ -227,7 +260,7 @@ def run_ours(args, rank, ws, local):
     return {
         "value": value, "ms": ms_max, "stats": st, "mode": head_kw["mode"], "opts": head_kw,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic("k_engine_fib22_frontier"),
                      "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": nbytes},
         "plain": {"ms": plain_ms, "value": rewrites / (plain_ms / 1e3),
                   "sweeps": plain_st["sweeps"], "visits": plain_st["visits"]},

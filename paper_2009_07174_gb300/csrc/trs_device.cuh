@@ -186,12 +186,47 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
     return D_MARK;
 }
 
-// Warp-aggregated allocation of m new slots per lane (Sec. 3, get_new_index):
-// one atomic per warp on the free-ring claim counter; claims past the slots
-// available in the ring overflow to fresh slots above the high-water mark,
-// again with one atomic per warp.  All 32 lanes must call.
-__device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc *A, int m,
-                                           int32_t *out)
+// Allocation (Sec. 3, get_new_index).  Every new node takes the next position
+// of one allocation sequence per sweep: positions below avail = fe - fb name
+// the free ring's entries, later ones the fresh slots n, n+1, ... above the
+// high-water mark.  A warp claims positions in chunks of kAllocChunk with one
+// atomic (warp-uniform state in WarpAlloc) and hands them to its lanes; the
+// positions a warp did not use are returned at the end of the phase (fresh
+// ones stamped free) and join the ring behind its end.
+constexpr int kAllocChunk = 128;
+
+struct WarpAlloc {
+    unsigned long long pos, end;  // unused positions [pos, end) of this warp
+    unsigned long long chunk;     // claim size (0: exactly what is needed)
+};
+
+// Chunk size for this sweep: all warps' leftovers together stay below half of
+// the ring cells this sweep does not read, so returned entries (written behind
+// fe during the sweep) never land on a cell that is still to be read; tiny
+// stores claim exactly.
+__device__ __forceinline__ WarpAlloc warp_alloc_begin(const DevPool &P, const State &S)
+{
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long room = (P.cap - (S.fe - S.fb)) / 2;
+    long long c = room / (warps > 0 ? warps : 1);
+    if (c > kAllocChunk) c = kAllocChunk;
+    if (c < 2) c = 0;
+    return WarpAlloc{0, 0, (unsigned long long)c};
+}
+
+__device__ __forceinline__ int32_t alloc_slot(const DevPool &P, const State &S, unsigned long long pos,
+                                              bool &ok)
+{
+    const long long avail = S.fe - S.fb;
+    if ((long long)pos < avail) return P.ring[(S.fb + (long long)pos) % P.cap];
+    const long long s = S.n + ((long long)pos - avail);
+    if (s >= P.cap) { ok = false; return 0; }
+    return (int32_t)s;
+}
+
+// m new slots for each lane (all 32 lanes call).
+__device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc *A, WarpAlloc &W,
+                                           int m, int32_t *out)
 {
     const int lane = threadIdx.x & 31;
     int x = m;
@@ -200,34 +235,60 @@ __device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc
         int y = __shfl_up_sync(kFull, x, o);
         if (lane >= o) x += y;
     }
-    int total = __shfl_sync(kFull, x, 31);
+    const int total = __shfl_sync(kFull, x, 31);
     if (total == 0) return true;
-    int excl = x - m;
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(&A->fl_claims, (unsigned long long)total);
-    base = __shfl_sync(kFull, base, 31);
-    const long long avail = S.fe - S.fb;
-    long long lo = (long long)base, hi = (long long)base + total;
-    long long fresh_from = lo > avail ? lo : avail;
-    long long wfresh = hi > fresh_from ? hi - fresh_from : 0;
-    unsigned long long fbase = 0;
-    if (lane == 31 && wfresh > 0) fbase = atomicAdd(&A->fresh, (unsigned long long)wfresh);
-    fbase = __shfl_sync(kFull, fbase, 31);
+    const int excl = x - m;
+    const unsigned long long have = W.end - W.pos;
+    unsigned long long nb = 0, nsize = 0;
+    if ((unsigned long long)total > have) {
+        nsize = (unsigned long long)(total - (int)have);
+        if (nsize < W.chunk) nsize = W.chunk;
+        if (lane == 0) nb = atomicAdd(&A->fl_claims, nsize);
+        nb = __shfl_sync(kFull, nb, 0);
+    }
     bool ok = true;
     for (int j = 0; j < m; j++) {
-        long long pos = lo + excl + j;
-        int32_t idx;
-        if (pos < avail) {
-            idx = P.ring[(S.fb + pos) % P.cap];
-        } else {
-            long long s = S.n + (long long)fbase + (pos - fresh_from);
-            if (s >= P.cap) { ok = false; idx = 0; }
-            else idx = (int32_t)s;
-        }
-        out[j] = idx;
+        const unsigned long long q = (unsigned long long)(excl + j);
+        const unsigned long long pos = q < have ? W.pos + q : nb + (q - have);
+        out[j] = alloc_slot(P, S, pos, ok);
+    }
+    if ((unsigned long long)total > have) {
+        W.pos = nb + ((unsigned long long)total - have);
+        W.end = nb + nsize;
+    } else {
+        W.pos += (unsigned long long)total;
     }
     if (!ok) set_status(P.ctl, TRS_ERR_POOL_FULL);
     return ok;
+}
+
+// End of a phase: give the warp's unused positions back (all 32 lanes call).
+__device__ __forceinline__ void warp_alloc_return(const DevPool &P, const State &S, Acc *A,
+                                                  WarpAlloc &W)
+{
+    const int lane = threadIdx.x & 31;
+    const long long avail = S.fe - S.fb;
+    // positions at or past `limit` would be fresh slots beyond the store:
+    // they were never usable and are not given back
+    const long long limit = avail + (P.cap - S.n);
+    long long cnt = (long long)(W.end - W.pos);
+    if ((long long)W.pos + cnt > limit) cnt = limit - (long long)W.pos;
+    if (cnt <= 0) { W.pos = W.end; return; }
+    unsigned long long rb = 0;
+    if (lane == 0) rb = atomicAdd(&A->ret, (unsigned long long)cnt);
+    rb = __shfl_sync(kFull, rb, 0);
+    for (long long q = lane; q < cnt; q += 32) {
+        const unsigned long long pos = W.pos + (unsigned long long)q;
+        int32_t slot;
+        if ((long long)pos < avail) {
+            slot = P.ring[(S.fb + (long long)pos) % P.cap];
+        } else {
+            slot = (int32_t)(S.n + ((long long)pos - avail));
+            P.nfs[slot] = 0;            // never used: a free slot below the new mark
+        }
+        P.ring[(S.fe + (long long)rb + q) % P.cap] = slot;
+    }
+    W.pos = W.end;
 }
 
 // Warp-aggregated append of cnt entries per lane to a frontier buffer.
@@ -259,9 +320,8 @@ __device__ __forceinline__ void warp_push(int32_t *buf, unsigned long long *coun
 // parent loses one pending argument; the notifier that takes the count to 0
 // owns the parent's next visit.  A unary parent has no other argument, so no
 // atomic is needed.
-__device__ __forceinline__ void notify_parent(const DevPool &P, int32_t i, int32_t *push, int &npush)
+__device__ __forceinline__ void notify_parent(const DevPool &P, int32_t pv, int32_t *push, int &npush)
 {
-    const int32_t pv = P.par[i];
     const int32_t p = pv & 0x7fffffff;
     if (p == 0) return;
     if (pv < 0 || atom_acqrel_add_s32(&P.pend[p], -1) == 1) push[npush++] = p;
@@ -295,16 +355,16 @@ __device__ __forceinline__ int32_t build_sym(const int32_t *build, int root_narg
 // consumed arguments are decremented) or record that i is in normal form.
 // Nodes to visit in the next sweep are appended to push[] (frontier modes).
 __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, int32_t i,
-                                      int32_t h, int r, long long k, const int32_t *reg,
+                                      int32_t h, int32_t pv, int r, long long k, const int32_t *reg,
                                       const int32_t *nw, Counters &C, int32_t *push, int &npush)
 {
     const long long cap = P.cap;
     if (r == D_MARK) {
         P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
         C.nf_marks++;
-        if (mode == M_FRONTIER) notify_parent(P, i, push, npush);
+        if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
         if (mode == M_LEARNED) {
-            const int32_t p = P.par[i] & 0x7fffffff;   // the parent may be ready now
+            const int32_t p = pv & 0x7fffffff;   // the parent may be ready now
             if (p != 0) learned_push(P, p, k + 1, push, npush);
         }
         if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
@@ -370,9 +430,9 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         P.hs[i] = xh;
         for (int a = 0; a < xa; a++) P.args[a * cap + i] = xc[a];
         P.nfs[i] = (int32_t)(k + 1);
-        if (mode == M_FRONTIER) notify_parent(P, i, push, npush);
+        if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
         if (mode == M_LEARNED) {
-            const int32_t p = P.par[i] & 0x7fffffff;
+            const int32_t p = pv & 0x7fffffff;
             if (p != 0) learned_push(P, p, k + 1, push, npush);
         }
     } else {
@@ -422,9 +482,9 @@ __device__ __forceinline__ void flush_counters(Counters &C, Acc *A)
 // One decision + allocation + application + push for every lane of a warp
 // (lane-uniform control flow; `cand` marks lanes with a node to consider).
 __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, const State &S,
-                                                Acc *A, int mode, bool cand, bool keep, int32_t i,
-                                                bool check_ready, int32_t *next_buf, Counters &C,
-                                                bool eager = false)
+                                                Acc *A, WarpAlloc &W, int mode, bool cand, bool keep,
+                                                int32_t i, bool check_ready, int32_t *next_buf,
+                                                Counters &C, bool eager = false)
 {
     int32_t reg[TRS_MAX_PATTERN];
     int32_t nw[TRS_MAX_RHS];
@@ -433,6 +493,9 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     int d = D_NONE;
     int32_t h = 0;
     if (keep) learned_push(P, i, S.k + 1, push, npush);  // learned: not yet eligible, keep it
+    // the parent word is loaded together with the node (it is needed when the
+    // node turns out to be a normal form), not after the decision
+    const int32_t pv = (mode != M_PLAIN && cand) ? P.par[i] : 0;
     if (cand) {
         C.visits++;
         d = decide(P, T, i, S.k, check_ready, reg, h);
@@ -440,9 +503,9 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     }
     int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;
     if (__any_sync(kFull, m > 0)) {
-        if (!warp_alloc(P, S, A, m, nw)) d = D_NONE;
+        if (!warp_alloc(P, S, A, W, m, nw)) d = D_NONE;
     }
-    if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, d, S.k, reg, nw, C, push, npush);
+    if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush);
     // eager continuation: keep one of the nodes that just became ready (the
     // last pushed: the redex itself, else its parent, else a new node) and
     // process it at once instead of in the next sweep
@@ -463,6 +526,7 @@ __device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, cons
                             long long warp0, long long nwarps)
 {
     Counters C{0, 0, 0, 0, 0};
+    WarpAlloc W = warp_alloc_begin(P, S);
     const int lane = threadIdx.x & 31;
     const long long n = S.n;
     const long long nchunks = (n + 127) / 128;
@@ -485,9 +549,10 @@ __device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, cons
 #pragma unroll 1
         for (int t = 0; t < 4; t++) {
             if (!__any_sync(kFull, any[t])) continue;
-            process_warp(P, T, S, A, M_PLAIN, any[t], false, (int32_t)(base + t), true, nullptr, C);
+            process_warp(P, T, S, A, W, M_PLAIN, any[t], false, (int32_t)(base + t), true, nullptr, C);
         }
     }
+    warp_alloc_return(P, S, A, W);
     flush_counters(C, A);
 }
 
@@ -501,6 +566,7 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                                long long warp0, long long nwarps, int eager = 0)
 {
     Counters C{0, 0, 0, 0, 0};
+    WarpAlloc W = warp_alloc_begin(P, S);
     const int lane = threadIdx.x & 31;
     const int32_t *cur = P.fq[S.cur];
     int32_t *next = P.fq[S.cur ^ 1];
@@ -521,7 +587,7 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                 }
             }
             if (!__any_sync(kFull, cand || keep)) continue;
-            process_warp(P, T, S, A, mode, cand, keep, i, mode == M_LEARNED, next, C);
+            process_warp(P, T, S, A, W, mode, cand, keep, i, mode == M_LEARNED, next, C);
         }
     } else {
         int32_t node = -1;
@@ -530,14 +596,15 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
         // stop following chains once this sweep's fresh allocations use half
         // of the slots still above the high-water mark: collection only runs
         // between sweeps
-        const unsigned long long fresh_budget = (unsigned long long)((P.cap - S.n) / 2);
+        const unsigned long long claim_budget =
+            (unsigned long long)((S.fe - S.fb) + (P.cap - S.n) / 2);
         bool pressure = false;
         int iter = 0;
         for (;;) {
             if ((++iter & 7) == 0 && !pressure) {
                 unsigned long long f = 0;
-                if (lane == 0) f = *(volatile unsigned long long *)&A->fresh;
-                pressure = __shfl_sync(kFull, f, 0) > fresh_budget;
+                if (lane == 0) f = *(volatile unsigned long long *)&A->fl_claims;
+                pressure = __shfl_sync(kFull, f, 0) > claim_budget;
             }
             const bool idle = node < 0;
             const unsigned im = __ballot_sync(kFull, idle);
@@ -563,13 +630,14 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                 if (drained) break;
                 continue;
             }
-            int32_t cont = process_warp(P, T, S, A, mode, cand, false, cand ? node : 0, false, next, C, true);
+            int32_t cont = process_warp(P, T, S, A, W, mode, cand, false, cand ? node : 0, false, next, C, true);
             steps++;
             const bool over = cont >= 0 && (steps >= eager || pressure);
             if (__any_sync(kFull, over)) warp_push(next, &A->pushes, P.cap, over ? 1 : 0, &cont, P.ctl);
             node = over ? -1 : cont;
         }
     }
+    warp_alloc_return(P, S, A, W);
     flush_counters(C, A);
 }
 

@@ -66,15 +66,15 @@ struct Program {
 // ---------------------------------------------------------------------------
 struct Acc {  // per-sweep accumulators, triple-buffered by sweep number % 3
     unsigned long long rewrites, nf_marks, visits, allocs;
-    unsigned long long fl_claims;  // free-ring positions claimed in this sweep
-    unsigned long long fresh;      // slots taken above the high-water mark
+    unsigned long long fl_claims;  // allocation positions claimed in this sweep
+    unsigned long long fresh;      // (unused)
     unsigned long long deaths;     // reference counts that reached zero
     unsigned long long pushes;     // entries written to the next frontier
     unsigned long long gc_frees, gc_deaths, gc_append;  // garbage collection
     unsigned long long conf_found, refresh_sel;
     unsigned long long taken;      // eager frontier sweep: entries claimed
     unsigned long long pending;    // learned refresh: live nodes not in normal form
-    unsigned long long pad[1];
+    unsigned long long ret;        // allocation positions given back (appended to the ring)
 };
 
 struct Ctl {

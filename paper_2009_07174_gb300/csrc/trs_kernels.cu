@@ -20,7 +20,7 @@ struct Flags {
 };
 
 struct AccVals {
-    unsigned long long rew, nfm, vis, alc, claims, fresh, deaths, pushes;
+    unsigned long long rew, nfm, vis, alc, claims, ret, deaths, pushes;
 };
 
 // Statistics of the running call, kept by thread 0 of block 0 and added to the
@@ -67,11 +67,11 @@ __device__ __forceinline__ AccVals read_acc(const Acc *A, bool in_smem)
         AccVals v;
         if (in_smem) {
             const volatile Acc *a = A;
-            v = AccVals{a->rewrites, a->nf_marks, a->visits, a->allocs, a->fl_claims, a->fresh,
+            v = AccVals{a->rewrites, a->nf_marks, a->visits, a->allocs, a->fl_claims, a->ret,
                         a->deaths, a->pushes};
         } else {
             v = AccVals{ldcg_u64(&A->rewrites), ldcg_u64(&A->nf_marks), ldcg_u64(&A->visits),
-                        ldcg_u64(&A->allocs), ldcg_u64(&A->fl_claims), ldcg_u64(&A->fresh),
+                        ldcg_u64(&A->allocs), ldcg_u64(&A->fl_claims), ldcg_u64(&A->ret),
                         ldcg_u64(&A->deaths), ldcg_u64(&A->pushes)};
         }
         s_v = v;
@@ -98,8 +98,14 @@ __device__ __forceinline__ unsigned long long read_u64_block(const unsigned long
 __device__ Flags end_sweep(State &S, const AccVals &V, const LaunchOpts &o, long long cap)
 {
     Flags F{false, false, false, false, false};
-    S.n += (long long)V.fresh;
-    S.fb = S.fb + (long long)V.claims < S.fe ? S.fb + (long long)V.claims : S.fe;
+    // the sweep's allocation positions: the first `avail` were ring entries,
+    // the rest fresh slots above the mark; unused ones came back behind fe
+    const long long avail = S.fe - S.fb;
+    const long long claims = (long long)V.claims;
+    S.n += claims > avail ? claims - avail : 0;
+    S.fb += claims < avail ? claims : avail;
+    S.fe += (long long)V.ret;
+    if (S.n > cap) S.n = cap;
     S.dead += (long long)V.deaths;
     const bool action = V.rew + V.nfm > 0;
     if (o.mode == M_PLAIN && !action) { F.done = true; return F; }

@@ -317,6 +317,52 @@ def msort_tree(lists) -> np.ndarray:
     return np.concatenate(parts).astype(np.int32)
 
 
+def msort_tree_uniform(values) -> np.ndarray:
+    """msort_tree for equal-length lists given as a 2-D array (one row per
+    list, a power-of-two number of rows), built with array operations only."""
+    vals = np.asarray(values, dtype=np.int64)
+    nl, ln = vals.shape
+    depth = int(nl).bit_length() - 1
+    if 1 << depth != nl:
+        raise ValueError("number of lists must be a power of two")
+    t = MSORT.id
+    # one leaf: Leaf, Sort, then per value Cons S^v Zero, then Nil
+    per_val = vals + 2
+    leaf_len = per_val.sum(axis=1) + 3
+    order = _heap_preorder(depth)
+    is_leaf = order >= nl
+    seg_len = np.where(is_leaf, leaf_len[np.where(is_leaf, order - nl, 0)], 1)
+    total = int(seg_len.sum())
+    out = np.empty(total, dtype=np.int32)
+    starts = np.cumsum(seg_len) - seg_len
+    out[starts[~is_leaf]] = t["Node"]
+    ls = starts[is_leaf]                        # leaf starts, in preorder of leaves
+    leaf_ids = order[is_leaf] - nl
+    out[ls] = t["Leaf"]
+    out[ls + 1] = t["Sort"]
+    # value blocks: Cons at the block start, S elsewhere, Zero at the block end
+    v = vals[leaf_ids]                          # values in preorder of leaves
+    pv = per_val[leaf_ids]
+    block_off = np.cumsum(pv, axis=1) - pv      # offset of each block inside its leaf
+    bstart = (ls[:, None] + 2 + block_off).ravel()
+    blen = pv.ravel()
+    idx = np.repeat(bstart, blen) + (np.arange(int(blen.sum())) -
+                                     np.repeat(np.cumsum(blen) - blen, blen))
+    out[idx] = t["S"]
+    out[bstart] = t["Cons"]
+    out[bstart + blen - 1] = t["Zero"]
+    out[ls + leaf_len[leaf_ids] - 1] = t["Nil"]
+    return out
+
+
+def msort_uniform_batch(seed: int = 0, depth: int = 23, length: int = 5, vmax: int = 9):
+    """The tree merge sort workload at paper scale: 2^depth lists of `length`
+    numerals uniform in [0, vmax] in a complete Node tree."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    vals = rng.integers(0, vmax + 1, size=(1 << depth, length))
+    return msort_tree_uniform(vals), vals
+
+
 def msort_batch(seed: int = 0, nlists: int = 256, lmin: int = 64, lmax: int = 1024,
                 vmax: int = 31):
     """One merge-sort input term: `nlists` lists (length uniform in [lmin, lmax],
