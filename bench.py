@@ -240,6 +240,8 @@ def run_ours(args, rank, ws, local):
     learned_kw = autotune_defaults("learned", "fib22")
     learned_ms, learned_st = timed(learned_kw, 3, 1)
 
+    scan = plain_scan_roofline()
+
     # end to end through the C ABI with host buffers: upload, normalise, download
     e2e_times = []
     h2d = d2h = 0
@@ -269,9 +271,46 @@ def run_ours(args, rank, ws, local):
                     "refreshes": learned_st["refreshes"], "train_rows": info["rows"],
                     "train_loss": [round(info["losses"][0], 4), round(info["losses"][-1], 4)]},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "plain_scan": scan,
         "clocks": clk.summary(),
         "gpu_launches": 2 * args.steps,
     }
+
+
+def plain_scan_roofline(reps=5):
+    """HBM side of the plain sweep: a store of 2048 arithmetic trees already in
+    normal form (a high-water mark of over 10^8 slots, stamps far larger
+    than L2); one plain normalisation is then a single sweep that streams every
+    stamp and finds nothing to do.  Bytes = 4 per slot below the mark."""
+    import torch
+    import paper_2009_07174_gb300 as trs
+    from paper_2009_07174_gb300 import autotune
+    t, build, cap = autotune.workloads()["arith-2048"]
+    flat, offs = build()
+    prog = trs.trs_compile(t)
+    pool = trs.Pool(prog, cap)
+    pool.term_upload_batch(flat, offs)
+    pool.trs_normalize(mode="frontier", eager=64)
+    n = pool.trs_pool_stats()["high_water"]
+    times = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pool.trs_normalize(wait=False, mode="plain")
+        e1.record()
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    st = pool.trs_pool_stats()
+    assert st["rewrites"] == 0 and st["sweeps"] == 0
+    ms = statistics.median(times)
+    peak, kind = peaks()
+    gbs = n * 4 / (ms / 1e3) / 1e9
+    del pool
+    return {"slots": n, "ms": ms, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_kind": f"{kind} hbm_gbs", "workload": "2048 arithmetic trees in normal form, pool 2^28",
+            "traffic": profiled_traffic("k_engine_plain_scan")}
 
 
 def cpu_baseline(target_s=10.0):
@@ -299,7 +338,10 @@ PROFILE_CASES = {
     "fib-batch-plain": ("fib-batch", 1 << 26, {"mode": "plain", "max_sweeps": 64}),
     "arith-frontier": ("arith", 1 << 26, None),
     "ttree-frontier": ("ttree", 1 << 24, None),
+    # a store already in normal form: the plain sweep is one streaming scan
+    "arith-plain-scan": ("arith-768", 1 << 26, {"mode": "plain"}),
 }
+PRE_NORMALISE = {"arith-plain-scan": {"mode": "frontier", "eager": 64}}
 
 
 def run_case(name, reps):
@@ -317,6 +359,8 @@ def run_case(name, reps):
     for _ in range(reps):
         pool.trs_pool_reset()
         pool.term_upload_batch(flat, offs)
+        if name in PRE_NORMALISE:
+            pool.trs_normalize(**PRE_NORMALISE[name])
         try:
             st = pool.trs_normalize(**kw)
         except trs.TrsError as e:
@@ -384,7 +428,7 @@ def main():
         "speedup_vs_plain": r["plain"]["ms"] / r["ms"],
         "learned_speedup_vs_plain": r["plain"]["ms"] / r["learned"]["ms"],
         "sweeps": st["sweeps"], "rewrites": st["rewrites"],
-        "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"],
+        "roofline": r["roofline"], "plain_scan": r["plain_scan"], "cpu_baseline": cb, "e2e": r["e2e"],
         "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
     }
     print(json.dumps(line))

@@ -142,6 +142,8 @@ def workloads():
         "fib22": (ti.FIB, lambda: ti.concat_terms([ti.fib_term(22)]), 1 << 24),
         "fib-batch": (ti.FIB, lambda: ti.fib_batch(0, 2000)[:2], 1 << 26),
         "arith": (ti.ARITH, lambda: ti.arith_batch(0, 128, 10, 12)[:2], 1 << 26),
+        "arith-768": (ti.ARITH, lambda: ti.arith_batch(0, 768, 10, 12)[:2], 1 << 26),
+        "arith-2048": (ti.ARITH, lambda: ti.arith_batch(0, 2048, 10, 12)[:2], 1 << 28),
         "msort": (ti.MSORT, lambda: ti.concat_terms([ti.msort_batch(0, 16, 64, 256)[0]]), 1 << 24),
         "ttree": (ti.TTREE, lambda: ti.concat_terms([ti.ttree_term(20)]), 1 << 23),
     }

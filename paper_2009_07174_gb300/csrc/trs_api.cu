@@ -12,7 +12,7 @@
 
 namespace trs {
 // trs_kernels.cu
-size_t engine_smem_bytes(const DevPool &P);
+size_t engine_smem_bytes(const DevPool &P, int mode, int block);
 cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm);
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
                           unsigned long long cond, cudaStream_t stream);
@@ -341,7 +341,7 @@ static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, l
     kp.func = engine_kernel_ptr(o.mode);
     kp.gridDim = dim3((unsigned)o.grid);
     kp.blockDim = dim3((unsigned)o.block);
-    kp.sharedMemBytes = (unsigned)engine_smem_bytes(dp);
+    kp.sharedMemBytes = (unsigned)engine_smem_bytes(dp, o.mode, o.block);
     kp.kernelParams = kargs;
     cudaGraphNode_t kn;
     CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp), "kernel node");
@@ -372,7 +372,7 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
         d.mlp = predictor_block(pool->pred);
         d.mlp_bytes = (int32_t)predictor_block_bytes(pool->pred);
     }
-    const size_t smem = engine_smem_bytes(d);
+    const size_t smem = engine_smem_bytes(d, o.mode, o.block_size);
     int bps = 0;
     CK(engine_configure(o.mode, o.block_size, smem, &bps), "occupancy");
     if (bps <= 0) { set_error("trs_normalize: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
@@ -453,7 +453,7 @@ int trs_collect_samples(trs_pool *pool, const trs_opts *opts, int32_t period, fl
     d.samp_label = (float *)((char *)dev_samples + feat_b + ((size_t)cap * 4 + 255) / 256 * 256);
     d.samp_cap = cap;
     int bps = 0;
-    CK(engine_configure(o.mode, o.block_size, engine_smem_bytes(d), &bps), "occupancy");
+    CK(engine_configure(o.mode, o.block_size, engine_smem_bytes(d, o.mode, o.block_size), &bps), "occupancy");
     if (bps <= 0) { set_error("trs_collect_samples: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
     LaunchOpts lo{};
     lo.mode = o.mode;

@@ -144,16 +144,26 @@ enum { D_SKIP = -1, D_MARK = -2, D_NONE = -3 };
 
 __device__ __forceinline__ bool is_nf_at(int32_t s, long long k) { return s > 0 && s <= k; }
 
+// Content of a node this lane has just written (head and first arguments),
+// handed to the next step of an eager chain so that it need not be read back.
+constexpr int kCarryArgs = 4;
+struct Carry {
+    int32_t h;                  // 0: nothing carried
+    int32_t c[kCarryArgs];
+};
+
 // Readiness and rule dispatch for node i (Sec. 3, derive kernel: a node is
 // rewritten when it is live, not in normal form and all its arguments are in
 // normal form; the rules of its head are tried in order, Sec. 2).
 // Returns a rule slot, D_MARK (no rule matched: normal form) or D_SKIP.
 // reg[] receives the nodes matched by the pattern of the returned rule.
 __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i, long long k,
-                                      bool check_ready, int32_t *reg, int32_t &h_out)
+                                      bool check_ready, int32_t *reg, int32_t &h_out,
+                                      const Carry &cin)
 {
     const long long cap = P.cap;
-    int32_t h = P.hs[i];
+    const bool carried = cin.h != 0;
+    int32_t h = carried ? cin.h : P.hs[i];
     h_out = h;
     int ar = T.arity(h);
     if (check_ready) {
@@ -176,7 +186,8 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
         bool ok = true;
         for (int q = 1; q < npat; q++) {
             uint32_t w = (uint32_t)pat[q - 1];
-            int32_t node = P.args[(long long)((w >> 8) & 0xff) * cap + reg[w & 0xff]];
+            const int ap = (w >> 8) & 0xff, pr = w & 0xff;
+            int32_t node = (carried && pr == 0) ? cin.c[ap] : P.args[(long long)ap * cap + reg[pr]];
             reg[q] = node;
             uint32_t sym = w >> 16;
             if (sym != 0 && (uint32_t)P.hs[node] != sym) { ok = false; break; }
@@ -356,9 +367,11 @@ __device__ __forceinline__ int32_t build_sym(const int32_t *build, int root_narg
 // Nodes to visit in the next sweep are appended to push[] (frontier modes).
 __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, int32_t i,
                                       int32_t h, int32_t pv, int r, long long k, const int32_t *reg,
-                                      const int32_t *nw, Counters &C, int32_t *push, int &npush)
+                                      const int32_t *nw, Counters &C, int32_t *push, int &npush,
+                                      Carry &last)
 {
     const long long cap = P.cap;
+    last.h = 0;
     if (r == D_MARK) {
         P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
         C.nf_marks++;
@@ -389,9 +402,13 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         int32_t parent = (w1 & 0xffff) - 1, pj = w1 >> 16;
         int32_t x = nw[j];
         P.hs[x] = sym;
+        Carry cx;
+        cx.h = na <= kCarryArgs ? sym : 0;
         for (int a = 0; a < na; a++) {
             int32_t op = build[pos++];
-            P.args[a * cap + x] = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
+            const int32_t v = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
+            P.args[a * cap + x] = v;
+            if (a < kCarryArgs) cx.c[a] = v;
         }
         P.rc[x] = 1;
         P.nfs[x] = stamp_new;
@@ -399,9 +416,13 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         if (mode == M_LEARNED) {
             P.pend[x] = (int32_t)(k + 1);
             push[npush++] = x;
+            last.h = 0;
         } else {
             P.pend[x] = pj;
-            if (mode == M_FRONTIER && pj == 0) push[npush++] = x;
+            if (mode == M_FRONTIER && pj == 0) {
+                push[npush++] = x;
+                last = cx;
+            }
         }
     }
     // root that is a variable x: i becomes a copy of x (x is in normal form)
@@ -430,22 +451,32 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         P.hs[i] = xh;
         for (int a = 0; a < xa; a++) P.args[a * cap + i] = xc[a];
         P.nfs[i] = (int32_t)(k + 1);
+        const int before = npush;
         if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
         if (mode == M_LEARNED) {
             const int32_t p = pv & 0x7fffffff;
             if (p != 0) learned_push(P, p, k + 1, push, npush);
         }
+        if (npush != before) last.h = 0;
     } else {
         P.hs[i] = R[1];
+        Carry ci;
+        ci.h = root_nargs <= kCarryArgs ? R[1] : 0;
         for (int a = 0; a < root_nargs; a++) {
             int32_t op = build[a];
-            P.args[a * cap + i] = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
+            const int32_t v = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
+            P.args[a * cap + i] = v;
+            if (a < kCarryArgs) ci.c[a] = v;
         }
         if (mode == M_LEARNED) {
             learned_push(P, i, k + 1, push, npush);
+            last.h = 0;
         } else {
             P.pend[i] = root_pend;
-            if (mode == M_FRONTIER && root_pend == 0) push[npush++] = i;
+            if (mode == M_FRONTIER && root_pend == 0) {
+                push[npush++] = i;
+                last = ci;
+            }
         }
     }
     if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
@@ -484,7 +515,7 @@ __device__ __forceinline__ void flush_counters(Counters &C, Acc *A)
 __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, const State &S,
                                                 Acc *A, WarpAlloc &W, int mode, bool cand, bool keep,
                                                 int32_t i, bool check_ready, int32_t *next_buf,
-                                                Counters &C, bool eager = false)
+                                                Counters &C, bool eager, Carry &carry)
 {
     int32_t reg[TRS_MAX_PATTERN];
     int32_t nw[TRS_MAX_RHS];
@@ -498,19 +529,26 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     const int32_t pv = (mode != M_PLAIN && cand) ? P.par[i] : 0;
     if (cand) {
         C.visits++;
-        d = decide(P, T, i, S.k, check_ready, reg, h);
+        d = decide(P, T, i, S.k, check_ready, reg, h, carry);
         if (mode == M_LEARNED && d == D_SKIP) learned_push(P, i, S.k + 1, push, npush);  // still waiting
     }
     int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;
     if (__any_sync(kFull, m > 0)) {
         if (!warp_alloc(P, S, A, W, m, nw)) d = D_NONE;
     }
-    if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush);
+    Carry last;
+    last.h = 0;
+    if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush, last);
     // eager continuation: keep one of the nodes that just became ready (the
     // last pushed: the redex itself, else its parent, else a new node) and
-    // process it at once instead of in the next sweep
+    // process it at once instead of in the next sweep; when this lane wrote
+    // that node in this step, its content travels with it
     int32_t cont = -1;
-    if (eager && npush > 0) cont = push[--npush];
+    carry.h = 0;
+    if (eager && npush > 0) {
+        cont = push[--npush];
+        carry = last;
+    }
     if (mode != M_PLAIN && __any_sync(kFull, npush > 0))
         warp_push(next_buf, &A->pushes, P.cap, npush, push, P.ctl);
     return cont;
@@ -520,38 +558,66 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
 // phases
 
 // Plain sweep: visit every slot below the high-water mark (Sec. 3, derive
-// kernel launched for all n terms).  The stamp array is read as int4 (four
-// slots per lane per load, 512 contiguous bytes per warp).
+// kernel launched for all n terms).  The stamp array is streamed as int4,
+// kPlainUnroll loads per lane in flight (2 KiB per warp) before any of them is
+// inspected; slots that are free, in normal form or not yet eligible cost only
+// their 4 bytes.
+constexpr int kPlainUnroll = 4;
+
+template <int U>
+__device__ __forceinline__ void plain_chunks(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                                             WarpAlloc &W, Counters &C, long long warp0, long long nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    const long long n = S.n;
+    constexpr long long kWarpSlots = 128LL * U;
+    const long long nchunks = (n + kWarpSlots - 1) / kWarpSlots;
+    for (long long ch = warp0; ch < nchunks; ch += nwarps) {
+        int4 s4[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long base = ch * kWarpSlots + (long long)u * 128 + lane * 4;
+            if (base + 3 < n) {
+                s4[u] = __ldcs(reinterpret_cast<const int4 *>(P.nfs + base));
+            } else {
+                s4[u] = make_int4(0, 0, 0, 0);
+                if (base + 0 < n) s4[u].x = P.nfs[base + 0];
+                if (base + 1 < n) s4[u].y = P.nfs[base + 1];
+                if (base + 2 < n) s4[u].z = P.nfs[base + 2];
+            }
+        }
+#pragma unroll 1
+        for (int u = 0; u < U; u++) {
+            const long long base = ch * kWarpSlots + (long long)u * 128 + lane * 4;
+            const int32_t sv[4] = {s4[u].x, s4[u].y, s4[u].z, s4[u].w};
+            bool any[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) any[t] = sv[t] < 0 && -(long long)sv[t] <= S.k;
+            if (!__ballot_sync(kFull, any[0] || any[1] || any[2] || any[3])) continue;
+#pragma unroll 1
+            for (int t = 0; t < 4; t++) {
+                if (!__any_sync(kFull, any[t])) continue;
+                Carry none;
+                none.h = 0;
+                process_warp(P, T, S, A, W, M_PLAIN, any[t], false, (int32_t)(base + t), true, nullptr,
+                             C, false, none);
+            }
+        }
+    }
+}
+
+// A small store keeps one int4 load per lane so that its few chunks spread
+// over as many warps as possible; a large one keeps kPlainUnroll per lane in
+// flight.
 __device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, const State &S, Acc *A,
-                            long long warp0, long long nwarps)
+                                            long long warp0, long long nwarps)
 {
     Counters C{0, 0, 0, 0, 0};
     WarpAlloc W = warp_alloc_begin(P, S);
-    const int lane = threadIdx.x & 31;
-    const long long n = S.n;
-    const long long nchunks = (n + 127) / 128;
-    for (long long ch = warp0; ch < nchunks; ch += nwarps) {
-        long long base = ch * 128 + lane * 4;
-        int4 s4 = make_int4(0, 0, 0, 0);
-        if (base + 3 < n) {
-            s4 = *reinterpret_cast<const int4 *>(P.nfs + base);
-        } else {
-            if (base + 0 < n) s4.x = P.nfs[base + 0];
-            if (base + 1 < n) s4.y = P.nfs[base + 1];
-            if (base + 2 < n) s4.z = P.nfs[base + 2];
-        }
-        int32_t sv[4] = {s4.x, s4.y, s4.z, s4.w};
-        bool any[4];
-#pragma unroll
-        for (int t = 0; t < 4; t++) any[t] = sv[t] < 0 && -(long long)sv[t] <= S.k;
-        unsigned ball = __ballot_sync(kFull, any[0] || any[1] || any[2] || any[3]);
-        if (!ball) continue;
-#pragma unroll 1
-        for (int t = 0; t < 4; t++) {
-            if (!__any_sync(kFull, any[t])) continue;
-            process_warp(P, T, S, A, W, M_PLAIN, any[t], false, (int32_t)(base + t), true, nullptr, C);
-        }
-    }
+    if (S.n >= nwarps * 128LL * kPlainUnroll * 2)
+        plain_chunks<kPlainUnroll>(P, T, S, A, W, C, warp0, nwarps);
+    else
+        plain_chunks<1>(P, T, S, A, W, C, warp0, nwarps);
     warp_alloc_return(P, S, A, W);
     flush_counters(C, A);
 }
@@ -587,12 +653,16 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                 }
             }
             if (!__any_sync(kFull, cand || keep)) continue;
-            process_warp(P, T, S, A, W, mode, cand, keep, i, mode == M_LEARNED, next, C);
+            Carry none;
+            none.h = 0;
+            process_warp(P, T, S, A, W, mode, cand, keep, i, mode == M_LEARNED, next, C, false, none);
         }
     } else {
         int32_t node = -1;
         int steps = 0;
         bool drained = false;
+        Carry carry;
+        carry.h = 0;
         // stop following chains once this sweep's fresh allocations use half
         // of the slots still above the high-water mark: collection only runs
         // between sweeps
@@ -620,7 +690,7 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                     if (e < S.fsz) {
                         int32_t i = cur[e];
                         int32_t s = P.nfs[i];
-                        if (s < 0 && -(long long)s <= S.k) { node = i; fresh_entry = true; }
+                        if (s < 0 && -(long long)s <= S.k) { node = i; fresh_entry = true; carry.h = 0; }
                     }
                 }
             }
@@ -630,7 +700,8 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                 if (drained) break;
                 continue;
             }
-            int32_t cont = process_warp(P, T, S, A, W, mode, cand, false, cand ? node : 0, false, next, C, true);
+            int32_t cont = process_warp(P, T, S, A, W, mode, cand, false, cand ? node : 0, false, next, C,
+                                        true, carry);
             steps++;
             const bool over = cont >= 0 && (steps >= eager || pressure);
             if (__any_sync(kFull, over)) warp_push(next, &A->pushes, P.cap, over ? 1 : 0, &cont, P.ctl);

@@ -19,6 +19,7 @@ struct Flags {
     bool done, gc, confirm, stop, refresh;
 };
 
+
 struct AccVals {
     unsigned long long rew, nfm, vis, alc, claims, ret, deaths, pushes;
 };
@@ -173,7 +174,7 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
 {
     LaunchOpts o = o_in;
     o.mode = MODE;
-    extern __shared__ int32_t smem[];
+    extern __shared__ __align__(128) int32_t smem[];
     __shared__ Acc s_acc;
     __shared__ int s_flag;
     Ctl *ctl = P.ctl;
@@ -430,8 +431,10 @@ static void *engine_fn(int mode)
     return (void *)k_engine<M_LEARNED>;
 }
 
-size_t engine_smem_bytes(const DevPool &P)
+size_t engine_smem_bytes(const DevPool &P, int mode, int block)
 {
+    (void)mode;
+    (void)block;
     return mlp_up16((size_t)P.tab_words * sizeof(int32_t)) + (P.mlp ? (size_t)P.mlp_bytes : 0);
 }
 
@@ -449,7 +452,7 @@ cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budge
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)o.grid);
     cfg.blockDim = dim3((unsigned)o.block);
-    cfg.dynamicSmemBytes = engine_smem_bytes(P);
+    cfg.dynamicSmemBytes = engine_smem_bytes(P, o.mode, o.block);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

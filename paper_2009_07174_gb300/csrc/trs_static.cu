@@ -23,7 +23,7 @@
 #include "trs_engine.h"
 
 namespace trs {
-size_t engine_smem_bytes(const DevPool &P);
+size_t engine_smem_bytes(const DevPool &P, int mode, int block);
 cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm);
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
                           unsigned long long cond, cudaStream_t stream);
@@ -193,7 +193,7 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
                     std::to_string(cap - 1) + "-slot static node store", TRS_ERR_TOO_BIG);
     int sms = 0, bps = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = engine_configure(o.mode, o.block_size, engine_smem_bytes(d), &bps);
+    if (e == cudaSuccess) e = engine_configure(o.mode, o.block_size, engine_smem_bytes(d, o.mode, o.block_size), &bps);
     if (e != cudaSuccess || bps <= 0) return fail("trs_normalize_static: occupancy query failed", TRS_ERR_CUDA);
     LaunchOpts lo{};
     lo.mode = o.mode;

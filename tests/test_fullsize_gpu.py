@@ -132,12 +132,14 @@ def test_config5_merge_sort_full(trs):
 def test_ttree22_paper_headline(trs):
     """Transformation tree of depth 22 (Sec. 4 and appendix): Expand(Suc^22(Zero))
     becomes the complete Node tree with 2^22 End leaves after 28 * 2^22 - 1
-    rewrites (2^23 - 1 Expand steps, 26 letter steps per leaf)."""
+    rewrites (2^23 - 1 Expand steps, 26 letter steps per leaf).  The plain
+    sweep runs here over a store of several million slots with candidates in
+    every sweep, the large-store form of its stamp scan."""
     t = ti.TTREE
     prog = trs.trs_compile(t)
     n = 22
     expect = np.where(ti._heap_preorder(n) < (1 << n), t.id["Node"], t.id["End"]).astype(np.int32)
-    for kw in (dict(mode="frontier", eager=64), dict(mode="frontier")):
+    for kw in (dict(mode="frontier", eager=64), dict(mode="frontier"), dict(mode="plain")):
         pool = trs.Pool(prog, 1 << 24)
         r = pool.term_upload(ti.ttree_term(n))
         st = pool.trs_normalize(**kw)
