@@ -206,7 +206,29 @@ int compile_program(const trs_signature *sig, const trs_rule *rules, int32_t nru
     t.assign(8, 0);
     t[0] = kTabMagic; t[1] = nsym; t[2] = ma; t[3] = nrules;
     t[4] = (int32_t)t.size();
-    t.insert(t.end(), arity.begin(), arity.end());
+    // arity word: arity | prefetch plan << 8.  The plan of a head lists what
+    // its patterns read two levels down, so that the matcher can issue those
+    // loads together with the argument heads: bit a (a < 4) argument 0 of
+    // argument a, bit 4 + a its argument 1, bits 8 + a and 12 + a the head
+    // symbols of those two nodes, bit 16 + a the head symbol of argument a.
+    std::vector<int32_t> plan(nsym, 0);
+    for (const CRule &c : compiled) {
+        std::vector<int32_t> par(c.npat, 0), pos(c.npat, 0), depth(c.npat, 0);
+        for (int32_t q = 1; q < c.npat; q++) {
+            const uint32_t w = (uint32_t)c.pat[q - 1];
+            par[q] = (int32_t)(w & 0xff);
+            pos[q] = (int32_t)((w >> 8) & 0xff);
+            depth[q] = depth[par[q]] + 1;
+            if (depth[q] == 1 && pos[q] < 4 && (w >> 16) != 0) plan[c.head] |= 1 << (16 + pos[q]);
+            if (depth[q] != 2) continue;
+            const int32_t a = pos[par[q]], ap = pos[q];
+            const bool sym = (w >> 16) != 0;
+            if (a >= 4 || ap >= 2) continue;
+            plan[c.head] |= 1 << (4 * ap + a);
+            if (sym) plan[c.head] |= 1 << (8 + 4 * ap + a);
+        }
+    }
+    for (int32_t s = 0; s < nsym; s++) t.push_back(arity[s] | (plan[s] << 8));
     t[5] = (int32_t)t.size();
     std::vector<int32_t> first(nsym + 1, 0);
     for (const CRule &c : compiled) first[c.head + 1]++;

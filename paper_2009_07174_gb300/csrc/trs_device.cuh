@@ -104,7 +104,9 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, long long tim
 struct Tab {
     const int32_t *w;
     int off_ar, off_first, off_rules;
-    __device__ __forceinline__ int arity(int s) const { return w[off_ar + s]; }
+    __device__ __forceinline__ int arity(int s) const { return w[off_ar + s] & 0xff; }
+    // prefetch plan of head s: what its patterns read two levels down
+    __device__ __forceinline__ int plan(int s) const { return w[off_ar + s] >> 8; }
     __device__ __forceinline__ int first(int s) const { return w[off_first + s]; }
     __device__ __forceinline__ const int32_t *rule(int r) const { return w + off_rules + r * kRuleWords; }
 };
@@ -152,45 +154,133 @@ struct Carry {
     int32_t c[kCarryArgs];
 };
 
+// Element j of a small per-thread array, by selects (the array stays in
+// registers).
+template <int N>
+__device__ __forceinline__ int32_t pick(const int32_t (&v)[N], int j)
+{
+    int32_t x = v[0];
+#pragma unroll
+    for (int t = 1; t < N; t++)
+        if (j == t) x = v[t];
+    return x;
+}
+
+// A node index read where no node need be (an argument word of a node whose
+// arity is lower than the pattern assumed): any value is mapped into the
+// store, so that the speculative loads below stay in bounds.
+__device__ __forceinline__ int32_t in_store(int32_t x, long long cap)
+{
+    return (uint32_t)x < (uint32_t)cap ? x : 0;
+}
+
+constexpr int kPf = 2;  // arguments whose subterms are prefetched
+
 // Readiness and rule dispatch for node i (Sec. 3, derive kernel: a node is
 // rewritten when it is live, not in normal form and all its arguments are in
 // normal form; the rules of its head are tried in order, Sec. 2).
 // Returns a rule slot, D_MARK (no rule matched: normal form) or D_SKIP.
 // reg[] receives the nodes matched by the pattern of the returned rule.
+//
+// Memory-level parallelism: once the arguments are known, the heads of the
+// first kPf arguments and the second-level words the head's rules read (the
+// table's prefetch plan) are loaded together, and the heads of those
+// second-level nodes in one more step, so that a pattern of depth two costs
+// two dependent loads instead of one per pattern node and rule.
 __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i, long long k,
                                       bool check_ready, int32_t *reg, int32_t &h_out,
                                       const Carry &cin)
 {
     const long long cap = P.cap;
     const bool carried = cin.h != 0;
-    int32_t h = carried ? cin.h : P.hs[i];
+    // an uncarried node's first two argument words are read with its head
+    int32_t h, w0 = 0, w1 = 0;
+    if (carried) {
+        h = cin.h;
+    } else {
+        h = P.hs[i];
+        if (P.ma > 0) w0 = P.args[i];
+        if (P.ma > 1) w1 = P.args[cap + i];
+    }
     h_out = h;
-    int ar = T.arity(h);
-    if (check_ready) {
-        int32_t c[TRS_MAX_ARITY];
+    const int aw = T.w[T.off_ar + h];
+    const int ar = aw & 0xff, plan = aw >> 8;
+    const int r0 = T.first(h), r1 = T.first(h + 1);
+    if (!check_ready && r0 == r1) return D_MARK;
+    int32_t c[TRS_MAX_ARITY];
 #pragma unroll
-        for (int j = 0; j < TRS_MAX_ARITY; j++)
-            if (j < ar) c[j] = P.args[j * cap + i];
+    for (int j = 0; j < TRS_MAX_ARITY; j++) {
+        c[j] = 0;
+        if (j < ar)
+            c[j] = (carried && j < kCarryArgs) ? cin.c[j]
+                   : j == 0                    ? w0
+                   : j == 1                    ? w1
+                                               : P.args[j * cap + i];
+    }
+    if (check_ready) {
         bool ready = true;
 #pragma unroll
         for (int j = 0; j < TRS_MAX_ARITY; j++)
             if (j < ar && !is_nf_at(P.nfs[c[j]], k)) ready = false;
         if (!ready) return D_SKIP;
+        if (r0 == r1) return D_MARK;
     }
-    int r0 = T.first(h), r1 = T.first(h + 1);
+    int32_t hc[kPf], d0[kPf], d1[kPf], e0[kPf], e1[kPf];
+#pragma unroll
+    for (int a = 0; a < kPf; a++) {
+        hc[a] = d0[a] = d1[a] = e0[a] = e1[a] = 0;
+        if (a < ar) {
+            if ((plan >> (16 + a)) & 1) hc[a] = P.hs[c[a]];
+            if ((plan >> a) & 1) d0[a] = P.args[c[a]];
+            if ((plan >> (4 + a)) & 1) d1[a] = P.args[cap + c[a]];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < kPf; a++) {
+        d0[a] = in_store(d0[a], cap);
+        d1[a] = in_store(d1[a], cap);
+        if ((plan >> (8 + a)) & 1) e0[a] = P.hs[d0[a]];
+        if ((plan >> (12 + a)) & 1) e1[a] = P.hs[d1[a]];
+    }
     for (int r = r0; r < r1; r++) {
         const int32_t *R = T.rule(r);
         int npat = R[0] & 0xff;
         const int32_t *pat = T.w + R[2];
         reg[0] = i;
+        // argument position of every register that holds one of the first
+        // kPf arguments of the redex (15: any other register)
+        unsigned long long posw = ~0ull;
         bool ok = true;
         for (int q = 1; q < npat; q++) {
             uint32_t w = (uint32_t)pat[q - 1];
             const int ap = (w >> 8) & 0xff, pr = w & 0xff;
-            int32_t node = (carried && pr == 0) ? cin.c[ap] : P.args[(long long)ap * cap + reg[pr]];
+            const int32_t sym = (int32_t)(w >> 16);
+            int32_t node, hn = 0;
+            bool have = false;
+            if (pr == 0) {
+                node = pick(c, ap);
+                if (ap < kPf) {
+                    hn = pick(hc, ap);
+                    have = (plan >> (16 + ap)) & 1;
+                    posw &= ~(15ull << (4 * q)) | ((unsigned long long)ap << (4 * q));
+                }
+            } else {
+                const int a = (int)((posw >> (4 * pr)) & 15);
+                if (a < kPf && ap == 0 && ((plan >> a) & 1)) {
+                    node = pick(d0, a);
+                    if ((plan >> (8 + a)) & 1) { hn = pick(e0, a); have = true; }
+                } else if (a < kPf && ap == 1 && ((plan >> (4 + a)) & 1)) {
+                    node = pick(d1, a);
+                    if ((plan >> (12 + a)) & 1) { hn = pick(e1, a); have = true; }
+                } else {
+                    node = P.args[(long long)ap * cap + reg[pr]];
+                }
+            }
             reg[q] = node;
-            uint32_t sym = w >> 16;
-            if (sym != 0 && (uint32_t)P.hs[node] != sym) { ok = false; break; }
+            if (sym != 0) {
+                if (!have) hn = P.hs[node];
+                if (hn != sym) { ok = false; break; }
+            }
         }
         if (ok) return r;
     }
@@ -209,6 +299,7 @@ constexpr int kAllocChunk = 128;
 struct WarpAlloc {
     unsigned long long pos, end;  // unused positions [pos, end) of this warp
     unsigned long long chunk;     // claim size (0: exactly what is needed)
+    int32_t pre;                  // lane l: the ring slot at position pos + l, else -1
 };
 
 // Chunk size for this sweep: all warps' leftovers together stay below half of
@@ -222,7 +313,7 @@ __device__ __forceinline__ WarpAlloc warp_alloc_begin(const DevPool &P, const St
     long long c = room / (warps > 0 ? warps : 1);
     if (c > kAllocChunk) c = kAllocChunk;
     if (c < 2) c = 0;
-    return WarpAlloc{0, 0, (unsigned long long)c};
+    return WarpAlloc{0, 0, (unsigned long long)c, -1};
 }
 
 __device__ __forceinline__ int32_t alloc_slot(const DevPool &P, const State &S, unsigned long long pos,
@@ -235,7 +326,19 @@ __device__ __forceinline__ int32_t alloc_slot(const DevPool &P, const State &S, 
     return (int32_t)s;
 }
 
-// m new slots for each lane (all 32 lanes call).
+// Ring entry for position pos of this warp's range, read ahead of its use
+// (-1 where the position is a fresh slot or outside the range).
+__device__ __forceinline__ int32_t ring_ahead(const DevPool &P, const State &S, unsigned long long pos,
+                                              unsigned long long end)
+{
+    const long long avail = S.fe - S.fb;
+    if (pos >= end || (long long)pos >= avail) return -1;
+    return P.ring[(S.fb + (long long)pos) % P.cap];
+}
+
+// m new slots for each lane (all 32 lanes call).  Lane l keeps the ring entry
+// of the warp's l-th next position in a register, loaded after the previous
+// allocation, so that ring slots are handed out without waiting for memory.
 __device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc *A, WarpAlloc &W,
                                            int m, int32_t *out)
 {
@@ -258,16 +361,27 @@ __device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc
         nb = __shfl_sync(kFull, nb, 0);
     }
     bool ok = true;
-    for (int j = 0; j < m; j++) {
+    const int mmax = __reduce_max_sync(kFull, m);
+    for (int j = 0; j < mmax; j++) {
         const unsigned long long q = (unsigned long long)(excl + j);
-        const unsigned long long pos = q < have ? W.pos + q : nb + (q - have);
-        out[j] = alloc_slot(P, S, pos, ok);
+        const int32_t ahead = __shfl_sync(kFull, W.pre, (int)(q & 31));
+        if (j >= m) continue;
+        if (q < have && q < 32 && ahead >= 0) {
+            out[j] = ahead;
+        } else {
+            const unsigned long long pos = q < have ? W.pos + q : nb + (q - have);
+            out[j] = alloc_slot(P, S, pos, ok);
+        }
     }
     if ((unsigned long long)total > have) {
         W.pos = nb + ((unsigned long long)total - have);
         W.end = nb + nsize;
+        W.pre = ring_ahead(P, S, W.pos + lane, W.end);
     } else {
         W.pos += (unsigned long long)total;
+        const int src = lane + total;
+        const int32_t moved = __shfl_sync(kFull, W.pre, src < 32 ? src : 31);
+        W.pre = src < 32 ? moved : ring_ahead(P, S, W.pos + lane, W.end);
     }
     if (!ok) set_status(P.ctl, TRS_ERR_POOL_FULL);
     return ok;
@@ -431,9 +545,14 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     if (rootvar) {
         int32_t x = reg[R[1]];
         xh = P.hs[x];
+        // the first two argument words are read with the head (before the
+        // arity is known); words beyond the arity are not used
+        int32_t sp0 = 0, sp1 = 0;
+        if (P.ma > 0) sp0 = P.args[x];
+        if (P.ma > 1) sp1 = P.args[cap + x];
         xa = T.arity(xh);
         for (int a = 0; a < xa; a++) {
-            xc[a] = P.args[a * cap + x];
+            xc[a] = a == 0 ? sp0 : a == 1 ? sp1 : P.args[a * cap + x];
             atomicAdd(&P.rc[xc[a]], 1);
         }
     }
@@ -573,35 +692,41 @@ __device__ __forceinline__ void plain_chunks(const DevPool &P, const Tab &T, con
     constexpr long long kWarpSlots = 128LL * U;
     const long long nchunks = (n + kWarpSlots - 1) / kWarpSlots;
     for (long long ch = warp0; ch < nchunks; ch += nwarps) {
-        int4 s4[U];
+        // the stamps are reduced to one candidate bit per slot before any
+        // candidate is processed, so that only the mask stays live across
+        // the rewrite code and the loads are never spilled
+        unsigned mask = 0;
+        {
+            int4 s4[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const long long base = ch * kWarpSlots + (long long)u * 128 + lane * 4;
-            if (base + 3 < n) {
-                s4[u] = __ldcs(reinterpret_cast<const int4 *>(P.nfs + base));
-            } else {
-                s4[u] = make_int4(0, 0, 0, 0);
-                if (base + 0 < n) s4[u].x = P.nfs[base + 0];
-                if (base + 1 < n) s4[u].y = P.nfs[base + 1];
-                if (base + 2 < n) s4[u].z = P.nfs[base + 2];
+            for (int u = 0; u < U; u++) {
+                const long long base = ch * kWarpSlots + (long long)u * 128 + lane * 4;
+                if (base + 3 < n) {
+                    s4[u] = __ldcs(reinterpret_cast<const int4 *>(P.nfs + base));
+                } else {
+                    s4[u] = make_int4(0, 0, 0, 0);
+                    if (base + 0 < n) s4[u].x = P.nfs[base + 0];
+                    if (base + 1 < n) s4[u].y = P.nfs[base + 1];
+                    if (base + 2 < n) s4[u].z = P.nfs[base + 2];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int32_t sv[4] = {s4[u].x, s4[u].y, s4[u].z, s4[u].w};
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    if (sv[t] < 0 && -(long long)sv[t] <= S.k) mask |= 1u << (u * 4 + t);
             }
         }
+        if (!__any_sync(kFull, mask != 0)) continue;
 #pragma unroll 1
-        for (int u = 0; u < U; u++) {
-            const long long base = ch * kWarpSlots + (long long)u * 128 + lane * 4;
-            const int32_t sv[4] = {s4[u].x, s4[u].y, s4[u].z, s4[u].w};
-            bool any[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++) any[t] = sv[t] < 0 && -(long long)sv[t] <= S.k;
-            if (!__ballot_sync(kFull, any[0] || any[1] || any[2] || any[3])) continue;
-#pragma unroll 1
-            for (int t = 0; t < 4; t++) {
-                if (!__any_sync(kFull, any[t])) continue;
-                Carry none;
-                none.h = 0;
-                process_warp(P, T, S, A, W, M_PLAIN, any[t], false, (int32_t)(base + t), true, nullptr,
-                             C, false, none);
-            }
+        for (int b = 0; b < 4 * U; b++) {
+            const bool cand = (mask >> b) & 1;
+            if (!__any_sync(kFull, cand)) continue;
+            const long long slot = ch * kWarpSlots + (long long)(b >> 2) * 128 + lane * 4 + (b & 3);
+            Carry none;
+            none.h = 0;
+            process_warp(P, T, S, A, W, M_PLAIN, cand, false, (int32_t)slot, true, nullptr, C, false, none);
         }
     }
 }
@@ -670,11 +795,13 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
             (unsigned long long)((S.fe - S.fb) + (P.cap - S.n) / 2);
         bool pressure = false;
         int iter = 0;
+        // the claim counter is read every 4 steps and its value used 4 steps
+        // later, so that the read never stalls the chain
+        unsigned long long fl_seen = 0;
         for (;;) {
-            if ((++iter & 7) == 0 && !pressure) {
-                unsigned long long f = 0;
-                if (lane == 0) f = *(volatile unsigned long long *)&A->fl_claims;
-                pressure = __shfl_sync(kFull, f, 0) > claim_budget;
+            if ((++iter & 3) == 0 && !pressure) {
+                pressure = __shfl_sync(kFull, fl_seen, 0) > claim_budget;
+                if (lane == 0) fl_seen = *(volatile unsigned long long *)&A->fl_claims;
             }
             const bool idle = node < 0;
             const unsigned im = __ballot_sync(kFull, idle);

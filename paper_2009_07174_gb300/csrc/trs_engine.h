@@ -22,7 +22,7 @@ namespace trs {
 //
 //   word 0..7   header: magic, nsym, maxarity, nrules, off_arity, off_first,
 //               off_rules, total words
-//   arity[nsym]
+//   arity[nsym]          arity | prefetch plan << 8 (see trs_compile.cpp)
 //   first[nsym+1]        rules of head s are rule slots first[s] .. first[s+1]
 //   rules[nrules][RW]    per rule slot (in head-symbol order, textual order kept)
 //   streams              pattern steps, build program, refcount deltas

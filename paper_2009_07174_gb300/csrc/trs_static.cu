@@ -83,7 +83,7 @@ __global__ void k_static_upload(DevPool P, const int32_t *term, long long len, i
                                 int32_t *stk_next)
 {
     Ctl *c = P.ctl;
-    const int32_t *ar = P.tab + P.tab[4];
+    const int32_t *ar = P.tab + P.tab[4];  // arity in the low byte of each word
     const int32_t nsym = P.tab[1];
     P.hs[0] = 0;
     P.nfs[0] = 0;
@@ -105,9 +105,9 @@ __global__ void k_static_upload(DevPool P, const int32_t *term, long long len, i
             int32_t j = stk_next[sp - 1]++;
             P.args[(long long)j * P.cap + parent] = node;
             P.par[node] = parent;
-            if (stk_next[sp - 1] == ar[P.hs[parent]]) sp--;
+            if (stk_next[sp - 1] == (ar[P.hs[parent]] & 0xff)) sp--;
         }
-        if (ar[s] > 0) { stk_node[sp] = node; stk_next[sp] = 0; sp++; }
+        if ((ar[s] & 0xff) > 0) { stk_node[sp] = node; stk_next[sp] = 0; sp++; }
     }
     if (sp != 0) { c->status = TRS_ERR_BAD_TERM; return; }
     c->sweep_id = 1;
@@ -131,7 +131,7 @@ __global__ void k_static_download(DevPool P, int32_t *out, long long out_cap, lo
         const int32_t s = P.hs[x];
         if (n >= out_cap) { c->status = TRS_ERR_BUFFER_SMALL; *out_len = -1; return; }
         out[n++] = s;
-        for (int a = ar[s] - 1; a >= 0; a--) {
+        for (int a = (ar[s] & 0xff) - 1; a >= 0; a--) {
             if (sp >= P.cap) { c->status = TRS_ERR_BUFFER_SMALL; *out_len = -1; return; }
             stk[sp++] = P.args[(long long)a * P.cap + x];
         }
