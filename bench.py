@@ -132,10 +132,12 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def profiled_traffic(name):
+def profiled_traffic(name, units=None):
     """DRAM bytes per launch recorded in profiles/<name>.md by an ncu capture
     (dram__bytes_read.sum + dram__bytes_write.sum), or None when the kernel
-    sources changed since that capture."""
+    sources changed since that capture.  When the capture ran a smaller case
+    of the same launch (its `units_per_launch` differs from `units`), the
+    bytes are scaled by the ratio of units."""
     path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
         return None
@@ -147,8 +149,11 @@ def profiled_traffic(name):
     if vals.get("source_sha256") != kernel_source_hash():
         return None
     try:
-        return int(float(vals["traffic_bytes_per_launch"]))
-    except (KeyError, ValueError):
+        traffic = float(vals["traffic_bytes_per_launch"])
+        if units is not None and "units_per_launch" in vals:
+            traffic *= units / float(vals["units_per_launch"])
+        return int(traffic)
+    except (KeyError, ValueError, ZeroDivisionError):
         return None
 
 
@@ -310,7 +315,7 @@ def plain_scan_roofline(reps=5):
     del pool
     return {"slots": n, "ms": ms, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "peak_kind": f"{kind} hbm_gbs", "workload": "2048 arithmetic trees in normal form, pool 2^28",
-            "traffic": profiled_traffic("k_engine_plain_scan")}
+            "traffic": profiled_traffic("k_engine_plain_scan", units=n)}
 
 
 def cpu_baseline(target_s=10.0):
@@ -340,6 +345,10 @@ PROFILE_CASES = {
     "ttree-frontier": ("ttree", 1 << 24, None),
     # a store already in normal form: the plain sweep is one streaming scan
     "arith-plain-scan": ("arith-768", 1 << 26, {"mode": "plain"}),
+    # the full-size batches (pool 2^28, about 7 GB): single-pass counters only
+    "arith-4096-frontier": ("arith-4096", 1 << 28, {"mode": "frontier", "eager": 256, "solo_max": 512}),
+    "fib-batch-10000-frontier": ("fib-batch-10000", 1 << 28, {"mode": "frontier", "eager": 64,
+                                                              "block_size": 256}),
 }
 PRE_NORMALISE = {"arith-plain-scan": {"mode": "frontier", "eager": 64}}
 

@@ -62,7 +62,9 @@ typedef enum {
     TRS_ERR_BUFFER_SMALL = 13, /* output buffer too small; the required size is returned */
     TRS_ERR_CUDA = 14,         /* a CUDA runtime call failed (message in trs_last_error) */
     TRS_ERR_STATE = 15,        /* call not valid in the current state (e.g. dead root) */
-    TRS_ERR_NO_PREDICTOR = 16  /* learned mode without an attached, trained predictor */
+    TRS_ERR_NO_PREDICTOR = 16, /* learned mode without an attached, trained predictor */
+    TRS_ERR_JIT = 17           /* run-time compilation of a specialised engine failed
+                                  (NVRTC missing, or a compile error: trs_last_error) */
 } trs_status;
 
 /* Calling thread's message for the last failed call ("" if none). */
@@ -99,6 +101,35 @@ int trs_compile(const trs_signature *sig, const trs_rule *rules, int32_t nrules,
 void trs_program_free(trs_program *prog);
 /* Largest arity of the compiled signature (the number of argument arrays). */
 int32_t trs_program_maxarity(const trs_program *prog);
+
+/* Specialised engine (the paper's generated rewrite code, Sec. 3).  Writes the
+ * matcher and rewriter of every rule of `prog` as straight-line CUDA C++,
+ * compiles it with the engine's sweep loop by NVRTC for the current device
+ * (sm_XYa) and loads it; later trs_normalize calls on pools of `prog` in
+ * modes plain, frontier and learned with the persistent or host driver run it
+ * (results and counts are those of the table-driven engine; the graph driver
+ * and trs_collect_samples keep the table-driven kernel; trs_opts.generic = 1
+ * selects it explicitly).  `cache_dir` (may be NULL) keeps compiled images by
+ * content hash.  Needs libnvrtc at run time and the CUDA include directory
+ * ($TRS_CUDA_INCLUDE, $CUDA_HOME/include or /usr/local/cuda/include).  Takes
+ * seconds on a cache miss.  Not thread-safe for one program.  Returns TRS_OK,
+ * TRS_ERR_JIT (NVRTC missing, or a compile error in trs_last_error) or
+ * TRS_ERR_CUDA (no device, or the image did not load). */
+int trs_specialise(trs_program *prog, const char *cache_dir);
+
+/* 1 if trs_specialise succeeded for `prog`, else 0. */
+int trs_program_is_specialised(const trs_program *prog);
+
+/* The generated rule code of `prog` (NUL-terminated) into buf[0 .. cap);
+ * returns the size needed including the NUL, or -1 for a NULL program. */
+int64_t trs_specialised_source(const trs_program *prog, char *buf, int64_t cap);
+
+/* Generate and compile the specialised engine for compute capability `cc`
+ * (e.g. 103 for sm_103a) without loading it: no device needed.  The
+ * compiler's resource report is left in trs_last_error.  *image_bytes
+ * receives the size of the compiled image.  TRS_OK or TRS_ERR_JIT. */
+int trs_specialise_compile(const trs_program *prog, int32_t cc, const char *cache_dir,
+                           int64_t *image_bytes);
 
 /* ------------------------------------------------------------------------ */
 /* Node store ("pool")                                                        */
@@ -180,7 +211,9 @@ typedef struct {
                                 the same sweep (same results and counts, fewer
                                 sweeps); 0 = synchronous sweeps */
     int64_t time_limit_ns;   /* wall-clock limit of the whole call (TRS_ERR_TIMEOUT) */
-    int32_t reserved[4];
+    int32_t generic;         /* 1 = run the table-driven engine even when the program
+                                has a specialised one (trs_specialise) */
+    int32_t reserved[3];
 } trs_opts;
 
 /* Fill *opts with defaults (PLAIN, PERSISTENT, 512 threads, spin-wait limit
@@ -204,7 +237,9 @@ typedef struct {
     int64_t live_nodes;   /* high_water - free - dead; dead is counted from above
                              between collections, so this is a lower bound */
     int64_t solo_sweeps;  /* sweeps run by one block */
-    int64_t reserved[9];
+    int64_t specialised;  /* 1: the last normalisation ran the engine specialised to
+                             the program (trs_specialise), 0: the table-driven one */
+    int64_t reserved[8];
 } trs_stats;
 
 /* Normalise every live term of the pool.  Enqueued on `stream`.  If `stats`

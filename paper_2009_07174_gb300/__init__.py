@@ -26,6 +26,8 @@ __all__ = ["lib", "TrsError", "Program", "Pool", "trs_compile", "Opts", "Stats",
            "MODES", "DRIVERS", "STATUS"]
 
 LIB_PATH = _build.LIB
+# compiled specialised engines, by content hash (Program.specialise)
+SPEC_CACHE = os.environ.get("TRS_SPEC_CACHE", os.path.join(_build.OUT, "spec"))
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"paper_2009_07174_gb300: CUDA library {LIB_PATH} is not built; run "
@@ -37,7 +39,7 @@ STATUS = {0: "TRS_OK", 1: "TRS_ERR_ARG", 2: "TRS_ERR_LHS_VAR", 3: "TRS_ERR_RHS_V
           4: "TRS_ERR_NONLINEAR", 5: "TRS_ERR_ARITY", 6: "TRS_ERR_SYMBOL", 7: "TRS_ERR_MAXARITY",
           8: "TRS_ERR_TOO_BIG", 9: "TRS_ERR_BAD_TERM", 10: "TRS_ERR_POOL_FULL",
           11: "TRS_ERR_SWEEP_LIMIT", 12: "TRS_ERR_TIMEOUT", 13: "TRS_ERR_BUFFER_SMALL",
-          14: "TRS_ERR_CUDA", 15: "TRS_ERR_STATE", 16: "TRS_ERR_NO_PREDICTOR"}
+          14: "TRS_ERR_CUDA", 15: "TRS_ERR_STATE", 16: "TRS_ERR_NO_PREDICTOR", 17: "TRS_ERR_JIT"}
 CODE = {v: k for k, v in STATUS.items()}
 MODES = {"plain": 0, "frontier": 1, "learned": 2}
 DRIVERS = {"persistent": 0, "graph": 1, "host": 2}
@@ -58,14 +60,14 @@ class Opts(ctypes.Structure):
                 ("max_sweeps", _i64), ("timeout_ns", _i64), ("gc_min_dead", _i32),
                 ("gc_div", _i32), ("solo_max", _i32), ("graph_unroll", _i32), ("refresh", _i32),
                 ("threshold", ctypes.c_float), ("trace", _i32), ("eager", _i32),
-                ("time_limit_ns", _i64), ("reserved", _i32 * 4)]
+                ("time_limit_ns", _i64), ("generic", _i32), ("reserved", _i32 * 3)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, _i64) for n in (
         "status", "rewrites", "nf_marks", "sweeps", "visits", "allocs", "frees", "gc_runs",
         "confirm_sweeps", "confirm_found", "refreshes", "frontier_peak", "high_water",
-        "live_nodes", "solo_sweeps")] + [("reserved", _i64 * 9)]
+        "live_nodes", "solo_sweeps", "specialised")] + [("reserved", _i64 * 8)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
@@ -88,6 +90,10 @@ _sig("trs_compile", ctypes.c_int, ctypes.POINTER(Signature), ctypes.POINTER(Rule
      ctypes.POINTER(_vp))
 _sig("trs_program_free", None, _vp)
 _sig("trs_program_maxarity", _i32, _vp)
+_sig("trs_specialise", ctypes.c_int, _vp, ctypes.c_char_p)
+_sig("trs_program_is_specialised", ctypes.c_int, _vp)
+_sig("trs_specialised_source", _i64, _vp, ctypes.c_char_p, _i64)
+_sig("trs_specialise_compile", ctypes.c_int, _vp, _i32, ctypes.c_char_p, ctypes.POINTER(_i64))
 _sig("trs_pool_bytes", ctypes.c_int, _vp, _i64, ctypes.POINTER(_sz))
 _sig("trs_pool_create", ctypes.c_int, _vp, _i64, _vp, _sz, _vp, ctypes.POINTER(_vp))
 _sig("trs_pool_free", None, _vp)
@@ -162,6 +168,33 @@ class Program:
     @property
     def maxarity(self) -> int:
         return lib.trs_program_maxarity(self._h)
+
+    @property
+    def specialised(self) -> bool:
+        return bool(lib.trs_program_is_specialised(self._h))
+
+    def specialise(self, cache_dir: str | None = SPEC_CACHE) -> "Program":
+        """Compile the engine specialised to this program's rules
+        (trs_specialise); later normalisations of its pools run it."""
+        if cache_dir:
+            os.makedirs(cache_dir, exist_ok=True)
+        _check(lib.trs_specialise(self._h, cache_dir.encode() if cache_dir else None), "trs_specialise")
+        return self
+
+    def specialised_source(self) -> str:
+        """The generated rule code (trs_specialised_source)."""
+        n = lib.trs_specialised_source(self._h, None, 0)
+        buf = ctypes.create_string_buffer(int(n))
+        lib.trs_specialised_source(self._h, buf, n)
+        return buf.value.decode()
+
+    def compile_specialised(self, cc: int = 103, cache_dir: str | None = None) -> int:
+        """Compile (not load) the specialised engine for compute capability
+        `cc`; no GPU needed.  Returns the image size in bytes."""
+        b = _i64()
+        _check(lib.trs_specialise_compile(self._h, int(cc), cache_dir.encode() if cache_dir else None,
+                                          ctypes.byref(b)), "trs_specialise_compile")
+        return int(b.value)
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -146,6 +146,10 @@ def workloads():
         "arith-2048": (ti.ARITH, lambda: ti.arith_batch(0, 2048, 10, 12)[:2], 1 << 28),
         "msort": (ti.MSORT, lambda: ti.concat_terms([ti.msort_batch(0, 16, 64, 256)[0]]), 1 << 24),
         "ttree": (ti.TTREE, lambda: ti.concat_terms([ti.ttree_term(20)]), 1 << 23),
+        # full-size batch workloads (4096 arithmetic trees of depth 10..14;
+        # 10,000 fib(n), n uniform in [5, 20])
+        "arith-4096": (ti.ARITH, lambda: ti.arith_batch(0, 4096)[:2], 1 << 28),
+        "fib-batch-10000": (ti.FIB, lambda: ti.fib_batch(0, 10000)[:2], 1 << 28),
     }
 
 

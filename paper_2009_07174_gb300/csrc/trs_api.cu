@@ -13,9 +13,10 @@
 namespace trs {
 // trs_kernels.cu
 size_t engine_smem_bytes(const DevPool &P, int mode, int block);
-cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm);
+cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm, const void *fn = nullptr);
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
-                          unsigned long long cond, cudaStream_t stream);
+                          unsigned long long cond, cudaStream_t stream,
+                          const void *fn = nullptr);
 cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream);
 cudaError_t reset_launch(const DevPool &P, cudaStream_t stream);
 cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
@@ -46,6 +47,7 @@ struct trs_pool {
     GraphCache graph;
     LaunchOpts last{};
     int last_driver = 0;
+    int last_spec = 0;      // the last normalisation ran a specialised engine
     int32_t *act = nullptr;              // per-slot act[] (predictor traces)
     const trs_predictor *pred = nullptr; // learned mode
 };
@@ -301,7 +303,7 @@ static int validate_opts(const trs_opts *o)
     if (o->block_size != 128 && o->block_size != 256 && o->block_size != 512) return TRS_ERR_ARG;
     if (o->max_sweeps <= 0 || o->timeout_ns <= 0 || o->gc_div < 0 || o->gc_min_dead < 0 ||
         o->grid_blocks < 0 || o->solo_max < 0 || o->graph_unroll <= 0 || o->time_limit_ns <= 0 ||
-        o->eager < 0)
+        o->eager < 0 || o->generic < 0 || o->generic > 1)
         return TRS_ERR_ARG;
     return TRS_OK;
 }
@@ -372,9 +374,13 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
         d.mlp = predictor_block(pool->pred);
         d.mlp_bytes = (int32_t)predictor_block_bytes(pool->pred);
     }
+    // the engine specialised to this program's rules, when there is one (the
+    // graph driver's loop condition is cleared by the table-driven kernel)
+    const void *fn = nullptr;
+    if (!o.generic && pool->prog->spec && o.driver != TRS_DRIVER_GRAPH) fn = spec_kernel(pool->prog->spec, o.mode);
     const size_t smem = engine_smem_bytes(d, o.mode, o.block_size);
     int bps = 0;
-    CK(engine_configure(o.mode, o.block_size, smem, &bps), "occupancy");
+    CK(engine_configure(o.mode, o.block_size, smem, &bps, fn), "occupancy");
     if (bps <= 0) { set_error("trs_normalize: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
     int max_grid = bps * pool->num_sms;
     int grid = o.grid_blocks > 0 ? std::min(o.grid_blocks, max_grid) : max_grid;
@@ -393,9 +399,10 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
     lo.eager = o.mode == TRS_MODE_FRONTIER ? o.eager : 0;
     pool->last = lo;
     pool->last_driver = o.driver;
+    pool->last_spec = fn != nullptr;
     CK(prep_launch(pool->d.ctl, o.max_sweeps, o.mode != TRS_MODE_PLAIN ? 1 : 0, stream), "prepare");
     if (o.driver == TRS_DRIVER_PERSISTENT) {
-        CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream), "engine launch");
+        CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream, fn), "engine launch");
     } else if (o.driver == TRS_DRIVER_GRAPH) {
         int st = build_graph(pool, d, lo, o.graph_unroll);
         if (st != TRS_OK) return st;
@@ -404,7 +411,7 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
         // Sec. 3 main loop: launch one sweep, read the loop state back, repeat
         int hflags[2];
         for (;;) {
-            CK(engine_launch(d, lo, 1, 0ull, stream), "engine launch");
+            CK(engine_launch(d, lo, 1, 0ull, stream, fn), "engine launch");
             CK(cudaMemcpyAsync(&hflags[0], &pool->d.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, stream),
                "read done");
             CK(cudaMemcpyAsync(&hflags[1], &pool->d.ctl->status, sizeof(int), cudaMemcpyDeviceToHost, stream),
@@ -504,6 +511,7 @@ int trs_pool_stats(trs_pool *pool, trs_stats *s, trs_stream stream)
     // dead nodes are counted from above between collections: a lower bound
     s->live_nodes = (h.n_top - 1) - (h.fl_end - h.fl_begin) - h.dead;
     s->solo_sweeps = h.st_solo_sweeps;
+    s->specialised = pool->last_spec;
     if (h.status != 0) {
         set_error(std::string("trs_normalize: device status ") + std::to_string(h.status));
         return h.status;

@@ -286,7 +286,12 @@ int trs_compile(const trs_signature *sig, const trs_rule *rules, int32_t nrules,
     return TRS_OK;
 }
 
-void trs_program_free(trs_program *prog) { delete prog; }
+void trs_program_free(trs_program *prog)
+{
+    if (!prog) return;
+    trs::spec_free(prog->spec);
+    delete prog;
+}
 
 int32_t trs_program_maxarity(const trs_program *prog) { return prog ? prog->p.maxarity : -1; }
 

@@ -4,7 +4,9 @@
 // barrier.  Included by trs_kernels.cu only.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 #include <stdint.h>
 
 #include "trs_engine.h"
@@ -362,7 +364,9 @@ __device__ __forceinline__ bool warp_alloc(const DevPool &P, const State &S, Acc
     }
     bool ok = true;
     const int mmax = __reduce_max_sync(kFull, m);
-    for (int j = 0; j < mmax; j++) {
+#pragma unroll
+    for (int j = 0; j < TRS_MAX_RHS; j++) {
+        if (j >= mmax) break;
         const unsigned long long q = (unsigned long long)(excl + j);
         const int32_t ahead = __shfl_sync(kFull, W.pre, (int)(q & 31));
         if (j >= m) continue;
@@ -473,6 +477,20 @@ __device__ __forceinline__ int32_t build_sym(const int32_t *build, int root_narg
     return build[pos] & 0xffff;
 }
 
+// Record that node i is in normal form (no rule matched) in sweep k.
+__device__ __forceinline__ void apply_mark(const DevPool &P, int mode, int32_t i, int32_t pv, long long k,
+                                           Counters &C, int32_t *push, int &npush)
+{
+    P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
+    C.nf_marks++;
+    if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
+    if (mode == M_LEARNED) {
+        const int32_t p = pv & 0x7fffffff;   // the parent may be ready now
+        if (p != 0) learned_push(P, p, k + 1, push, npush);
+    }
+    if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
+}
+
 // Apply the decision for node i (rule slot r or D_MARK) in sweep k: rewrite in
 // place (Sec. 3, rewrite listing: the redex slot receives the right-hand side's
 // root, new nodes receive the other non-variable positions, variables are
@@ -487,14 +505,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     const long long cap = P.cap;
     last.h = 0;
     if (r == D_MARK) {
-        P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
-        C.nf_marks++;
-        if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
-        if (mode == M_LEARNED) {
-            const int32_t p = pv & 0x7fffffff;   // the parent may be ready now
-            if (p != 0) learned_push(P, p, k + 1, push, npush);
-        }
-        if (P.act) P.act[i] = min(P.act[i], (int32_t)k);
+        apply_mark(P, mode, i, pv, k, C, push, npush);
         return;
     }
     const int32_t *R = T.rule(r);
@@ -629,6 +640,19 @@ __device__ __forceinline__ void flush_counters(Counters &C, Acc *A)
     C = Counters{0, 0, 0, 0, 0};
 }
 
+#ifdef TRS_JIT
+// Rule matching and rewriting generated for one rule system: the same
+// contract as decide() and apply(), with the rules as straight-line code
+// (defined by the run-time compiled source after this header).
+__device__ __forceinline__ int spec_decide(const DevPool &P, const Tab &T, int32_t i, long long k,
+                                           bool check_ready, int32_t *reg, int32_t &h_out,
+                                           const Carry &cin);
+__device__ __forceinline__ void spec_apply(const DevPool &P, const Tab &T, int mode, int32_t i, int32_t h,
+                                           int32_t pv, int r, long long k, const int32_t *reg,
+                                           const int32_t *nw, Counters &C, int32_t *push, int &npush,
+                                           Carry &last);
+#endif
+
 // One decision + allocation + application + push for every lane of a warp
 // (lane-uniform control flow; `cand` marks lanes with a node to consider).
 __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, const State &S,
@@ -648,7 +672,11 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     const int32_t pv = (mode != M_PLAIN && cand) ? P.par[i] : 0;
     if (cand) {
         C.visits++;
+#ifdef TRS_JIT
+        d = spec_decide(P, T, i, S.k, check_ready, reg, h, carry);
+#else
         d = decide(P, T, i, S.k, check_ready, reg, h, carry);
+#endif
         if (mode == M_LEARNED && d == D_SKIP) learned_push(P, i, S.k + 1, push, npush);  // still waiting
     }
     int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;
@@ -657,7 +685,11 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     }
     Carry last;
     last.h = 0;
+#ifdef TRS_JIT
+    if (d >= 0 || d == D_MARK) spec_apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush, last);
+#else
     if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush, last);
+#endif
     // eager continuation: keep one of the nodes that just became ready (the
     // last pushed: the redex itself, else its parent, else a new node) and
     // process it at once instead of in the next sweep; when this lane wrote

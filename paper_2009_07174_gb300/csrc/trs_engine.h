@@ -3,8 +3,10 @@
 #pragma once
 
 #include <stdint.h>
+#ifndef __CUDACC_RTC__
 #include <string>
 #include <vector>
+#endif
 
 #include "../../include/trs.h"
 
@@ -51,6 +53,7 @@ constexpr int32_t kTabMagic = 0x54525331;  // "TRS1"
 constexpr int kRuleWords = 6;
 constexpr int kMaxTabWords = 12288;  // 48 KB of shared memory at most
 
+#ifndef __CUDACC_RTC__
 struct Program {
     int32_t nsym = 0;
     int32_t maxarity = 0;
@@ -60,6 +63,7 @@ struct Program {
     std::vector<int32_t> rule_orig;  // slot -> original rule index
     std::vector<uint8_t> has_rules;  // per symbol
 };
+#endif
 
 // ---------------------------------------------------------------------------
 // Device control block.
@@ -157,14 +161,24 @@ struct LaunchOpts {
     int32_t pad2;
 };
 
+#ifndef __CUDACC_RTC__
 // compile (host)
 int compile_program(const trs_signature *sig, const trs_rule *rules, int32_t nrules,
                     Program *out, std::string *err);
 
 void set_error(const std::string &msg);
 
+struct SpecEngine;  // the engine compiled for one program (trs_spec.cpp)
+void spec_free(SpecEngine *e);
+// kernel of the specialised engine for a mode (nullptr: none for this mode)
+const void *spec_kernel(const SpecEngine *e, int mode);
+#endif
+
 }  // namespace trs
 
+#ifndef __CUDACC_RTC__
 struct trs_program {
     trs::Program p;
+    trs::SpecEngine *spec = nullptr;
 };
+#endif

@@ -24,9 +24,9 @@
 
 namespace trs {
 size_t engine_smem_bytes(const DevPool &P, int mode, int block);
-cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm);
+cudaError_t engine_configure(int mode, int block, size_t smem, int *blocks_per_sm, const void *fn = nullptr);
 cudaError_t engine_launch(const DevPool &P, const LaunchOpts &o, long long budget,
-                          unsigned long long cond, cudaStream_t stream);
+                          unsigned long long cond, cudaStream_t stream, const void *fn = nullptr);
 cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
 
 namespace {

@@ -101,32 +101,6 @@ def test_brute_force_terms_batched(trs, t, size):
     check(trs, t, terms)
 
 
-X, Y, Z, A, B, C, D, E = (ti.Var(v) for v in "xyzabcde")
-WIDE = ti.TRS("wide", [("0", 0), ("S", 1), ("c", 2), ("g", 3), ("h", 4)], [
-    (("g", X, Y, "0"), X),
-    (("g", X, Y, ("S", Z)), ("g", ("S", X), Y, Z)),
-    (("h", ("S", ("S", A)), B, ("c", X, Y), ("S", D)), ("h", A, ("S", B), ("c", Y, X), D)),
-    (("h", "0", B, ("c", X, Y), D), ("g", B, D, X)),
-    (("h", ("S", "0"), B, E, D), ("g", D, B, "0")),
-])
-
-
-def wide_terms(seed, count, depth):
-    """Seeded random ground terms over WIDE (every symbol at every position)."""
-    rng = np.random.default_rng(seed)
-    names = ["0", "S", "c", "g", "h"]
-
-    def gen(d):
-        if d == 0:
-            return "0"
-        f = names[rng.integers(0, 5)]
-        ar = int(WIDE.arity[WIDE.id[f]])
-        if ar == 0:
-            return f
-        return (f, *(gen(d - 1) for _ in range(ar)))
-    return [WIDE.encode(gen(depth)) for _ in range(count)]
-
-
 def test_wide_patterns(trs):
     """Patterns that test arguments beyond the second, two and three levels
     down, in every argument position (the matcher's prefetched and plain
@@ -137,8 +111,8 @@ def test_wide_patterns(trs):
     fixed = [("h", n(4), "0", ("c", n(1), "0"), n(3)), ("h", "0", n(1), ("c", n(2), "0"), n(1)),
              ("h", n(1), "0", "0", n(1)), ("g", "0", "0", n(3)),
              ("h", n(5), ("g", "0", "0", n(2)), ("c", ("h", n(1), "0", "0", "0"), n(1)), n(6))]
-    check(trs, WIDE, [WIDE.encode(x) for x in fixed] + wide_terms(5, 300, 5))
-    check(trs, WIDE, wide_terms(6, 200, 6), modes=["frontier"], check_sweeps=False, eager=16)
+    check(trs, ti.WIDE, [ti.WIDE.encode(x) for x in fixed] + ti.wide_terms(5, 300, 5))
+    check(trs, ti.WIDE, ti.wide_terms(6, 200, 6), modes=["frontier"], check_sweeps=False, eager=16)
 
 
 def test_fib22_plain_and_frontier(trs):

@@ -371,3 +371,31 @@ def msort_batch(seed: int = 0, nlists: int = 256, lmin: int = 64, lmax: int = 10
     lens = rng.integers(lmin, lmax + 1, size=nlists)
     lists = [rng.integers(0, vmax + 1, size=int(k)) for k in lens]
     return msort_tree(lists), lists
+
+
+# A system with patterns beyond the second argument and three levels deep, in
+# every argument position (arities up to 4), for matcher coverage.
+_X, _Y, _Z, _A, _B, _C, _D, _E = (Var(v) for v in "xyzabcde")
+WIDE = TRS("wide", [("0", 0), ("S", 1), ("c", 2), ("g", 3), ("h", 4)], [
+    (("g", _X, _Y, "0"), _X),
+    (("g", _X, _Y, ("S", _Z)), ("g", ("S", _X), _Y, _Z)),
+    (("h", ("S", ("S", _A)), _B, ("c", _X, _Y), ("S", _D)), ("h", _A, ("S", _B), ("c", _Y, _X), _D)),
+    (("h", "0", _B, ("c", _X, _Y), _D), ("g", _B, _D, _X)),
+    (("h", ("S", "0"), _B, _E, _D), ("g", _D, _B, "0")),
+])
+
+
+def wide_terms(seed, count, depth):
+    """Seeded random ground terms over WIDE (every symbol at every position)."""
+    rng = np.random.default_rng(seed)
+    names = ["0", "S", "c", "g", "h"]
+
+    def gen(d):
+        if d == 0:
+            return "0"
+        f = names[rng.integers(0, 5)]
+        ar = int(WIDE.arity[WIDE.id[f]])
+        if ar == 0:
+            return f
+        return (f, *(gen(d - 1) for _ in range(ar)))
+    return [WIDE.encode(gen(depth)) for _ in range(count)]
