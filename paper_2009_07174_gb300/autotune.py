@@ -164,12 +164,15 @@ def main(argv=None):
     ap.add_argument("--modes", default="frontier,learned")
     ap.add_argument("--out", default=CACHE)
     ap.add_argument("-v", action="store_true")
+    ap.add_argument("--generic", action="store_true", help="tune the table-driven engine")
     a = ap.parse_args(argv)
     W = workloads()
     for name in a.workloads.split(","):
         t, build, cap = W[name]
         flat, offs = build()
         prog = trs.trs_compile(t)
+        if not a.generic:
+            prog.specialise()
         probe = trs.Pool(prog, cap)
         probe.term_upload_batch(flat, offs)
         expect = probe.trs_normalize(mode="frontier", eager=64)["rewrites"]

@@ -101,6 +101,14 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, long long tim
     return s_ok != 0;
 }
 
+// Reference-count change with no result: a relaxed reduction at GPU scope.
+// Nothing in a sweep reads the counts back (collection runs between sweeps,
+// after the grid barrier's fences), so the change need not return.
+__device__ __forceinline__ void red_add_s32(int32_t *p, int32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v));
+}
+
 // ---------------------------------------------------------------------------
 // staged rule table
 struct Tab {
@@ -564,7 +572,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         xa = T.arity(xh);
         for (int a = 0; a < xa; a++) {
             xc[a] = a == 0 ? sp0 : a == 1 ? sp1 : P.args[a * cap + x];
-            atomicAdd(&P.rc[xc[a]], 1);
+            red_add_s32(&P.rc[xc[a]], 1);
         }
     }
     // net reference changes of matched nodes, positive ones first; fire and
@@ -574,7 +582,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     for (int d = 0; d < ndelta; d++) {
         int32_t w = delta[d];
         int32_t q = w & 0xff, dv = w >> 8;
-        atomicAdd(&P.rc[reg[q]], dv);
+        red_add_s32(&P.rc[reg[q]], dv);
         if (dv < 0) C.deaths++;
     }
     if (rootvar) {
@@ -651,6 +659,8 @@ __device__ __forceinline__ void spec_apply(const DevPool &P, const Tab &T, int m
                                            int32_t pv, int r, long long k, const int32_t *reg,
                                            const int32_t *nw, Counters &C, int32_t *push, int &npush,
                                            Carry &last);
+// new slots a decision needs (its rule's new nodes less the reused slots)
+__device__ __forceinline__ int spec_new_count(int d);
 #endif
 
 // One decision + allocation + application + push for every lane of a warp
@@ -679,7 +689,11 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
 #endif
         if (mode == M_LEARNED && d == D_SKIP) learned_push(P, i, S.k + 1, push, npush);  // still waiting
     }
+#ifdef TRS_JIT
+    int m = (d >= 0) ? spec_new_count(d) : 0;
+#else
     int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;
+#endif
     if (__any_sync(kFull, m > 0)) {
         if (!warp_alloc(P, S, A, W, m, nw)) d = D_NONE;
     }

@@ -120,7 +120,41 @@ std::vector<PatNode> pattern_nodes(const RuleView &r)
 
 int arity_of(const Program &P, int s) { return (s > 0 && s < P.nsym) ? P.arity[s] : 0; }
 
-std::string operand(int32_t op) { return (op >> 16) ? "nw[" + std::to_string(op & 0xffff) + "]" : "reg[" + std::to_string(op & 0xffff) + "]"; }
+// Slot reuse: a constructor argument of the redex that the right-hand side
+// does not mention (net reference change -1) dies in the rewrite when the
+// redex held its only reference.  Its slot then takes one of the rule's new
+// nodes: no allocation, no decrement of it, and its arguments' references
+// move to the new nodes (each argument's net change drops by one), so nothing
+// is left for the collector.  Whether every paired argument has a count of 1
+// is read in the match (the count of a node referenced once cannot change
+// during the sweep: only a rewrite of its one parent could touch it), and the
+// rule then reuses all pairs or none.
+struct ReusePlan {
+    std::vector<int> cand;           // pattern registers whose slots are reused, paired with new nodes 0, 1, ...
+    std::vector<std::pair<int, int>> delta;  // (register, change) with reuse, positive first
+};
+
+ReusePlan reuse_plan(const RuleView &r)
+{
+    ReusePlan rp;
+    const std::vector<PatNode> ns = pattern_nodes(r);
+    std::map<int, int> dv;
+    for (int d = 0; d < r.ndelta; d++) dv[r.delta[d] & 0xff] = r.delta[d] >> 8;
+    for (int q = 1; q < r.npat && (int)rp.cand.size() < r.nnew; q++)
+        if (ns[q].parent == 0 && ns[q].sym != 0 && dv.count(q) && dv[q] == -1) rp.cand.push_back(q);
+    if (rp.cand.empty()) return rp;
+    std::map<int, int> adj = dv;
+    for (int c : rp.cand) adj.erase(c);
+    for (int q = 1; q < r.npat; q++)
+        for (int c : rp.cand)
+            if (ns[q].parent == c) adj[q] -= 1;
+    for (auto &e : adj)
+        if (e.second > 0) rp.delta.push_back(e);
+    for (auto &e : adj)
+        if (e.second < 0) rp.delta.push_back(e);
+    return rp;
+}
+
 
 void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, int last)
 {
@@ -149,8 +183,16 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
             if (n.path.size() == 1 && n.sym) sym1.insert(n.path);
             if (n.path.size() == 2) val2.insert(n.path);
         }
+    // argument positions whose counts decide a slot reuse
+    std::set<int> rcpos;
+    std::vector<ReusePlan> plans;
+    for (size_t ri = 0; ri < rules.size(); ri++) {
+        plans.push_back(reuse_plan(rules[ri]));
+        for (int q : plans.back().cand) rcpos.insert(nodes[ri][q].argpos);
+    }
     // level 1: argument heads and second-level words together
     for (auto &p : sym1) o << "        const int32_t " << sym_name(p) << " = P.hs[" << val_name(p) << "];\n";
+    for (int j : rcpos) o << "        const int32_t rc" << j << " = P.rc[c" << j << "];\n";
     for (auto &p : val2)
         o << "        const int32_t " << val_name(p) << " = in_store(P.args[" << p[1] << "LL * cap + c" << p[0]
           << "], cap);\n";
@@ -182,26 +224,44 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
         }
         o << "            reg[0] = i;\n";
         for (size_t q = 1; q < ns.size(); q++) o << "            reg[" << q << "] = " << val_name(ns[q].path) << ";\n";
-        o << "            return " << r.slot << ";\n        } while (0);\n";
+        if (plans[ri].cand.empty()) {
+            o << "            return " << r.slot << ";\n        } while (0);\n";
+        } else {
+            std::string u;
+            for (int q : plans[ri].cand) u += std::string(u.empty() ? "" : " && ") + "rc" + std::to_string(ns[q].argpos) + " == 1";
+            o << "            return " << r.slot << " | ((" << u << ") ? 0x10000 : 0);\n        } while (0);\n";
+        }
     }
     o << "        return D_MARK;\n    }\n";
 }
 
-void gen_apply_rule(std::ostringstream &o, const Program &P, const RuleView &r)
+void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, const ReusePlan *rp)
 {
-    o << "    case " << r.slot << ": {  // rule " << r.orig << "\n";
     int pos = r.root_nargs;
     std::vector<int> new_sym;
+    // the slot of new node j as an expression
+    auto new_slot = [&](int j) -> std::string {
+        const int np = rp ? (int)rp->cand.size() : 0;
+        return j < np ? "reg[" + std::to_string(rp->cand[j]) + "]" : "nw[" + std::to_string(j - np) + "]";
+    };
+    // an operand: a match register or the slot of a new node
+    auto opnd = [&](int32_t op) -> std::string {
+        return (op >> 16) ? new_slot(op & 0xffff) : "reg[" + std::to_string(op & 0xffff) + "]";
+    };
     for (int j = 0; j < r.nnew; j++) {
         const int32_t w0 = r.build[pos++], w1 = r.build[pos++];
         const int sym = w0 & 0xffff, na = w0 >> 16;
         const int parent = (w1 & 0xffff) - 1, pj = w1 >> 16;
         new_sym.push_back(sym);
-        o << "        {\n            const int32_t x = nw[" << j << "];\n";
+        const int npairs = rp ? (int)rp->cand.size() : 0;
+        if (j < npairs)
+            o << "        {\n            const int32_t x = reg[" << rp->cand[j] << "];\n";
+        else
+            o << "        {\n            const int32_t x = nw[" << j - npairs << "];\n";
         o << "            P.hs[x] = " << sym << ";\n";
         std::vector<std::string> ops;
         for (int a = 0; a < na; a++) {
-            ops.push_back(operand(r.build[pos++]));
+            ops.push_back(opnd(r.build[pos++]));
             o << "            P.args[" << a << "LL * cap + x] = " << ops.back() << ";\n";
         }
         o << "            P.rc[x] = 1;\n            P.nfs[x] = stamp_new;\n";
@@ -210,7 +270,7 @@ void gen_apply_rule(std::ostringstream &o, const Program &P, const RuleView &r)
             o << "            P.par[x] = i" << (un ? " | (int32_t)0x80000000" : "") << ";\n";
         } else {
             const bool un = arity_of(P, new_sym[parent]) == 1;
-            o << "            P.par[x] = nw[" << parent << "]" << (un ? " | (int32_t)0x80000000" : "") << ";\n";
+            o << "            P.par[x] = " << new_slot(parent) << (un ? " | (int32_t)0x80000000" : "") << ";\n";
         }
         o << "            if (mode == M_LEARNED) {\n                P.pend[x] = (int32_t)(k + 1);\n"
              "                push[npush++] = x;\n                last.h = 0;\n            } else {\n";
@@ -232,14 +292,18 @@ void gen_apply_rule(std::ostringstream &o, const Program &P, const RuleView &r)
         o << "        const int32_t x = reg[" << r.rootval << "];\n        const int32_t xh = P.hs[x];\n";
         for (int a = 0; a < ma; a++) o << "        int32_t xc" << a << " = P.args[" << a << "LL * cap + x];\n";
         o << "        const int xa = T.arity(xh);\n";
-        for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) atomicAdd(&P.rc[xc" << a << "], 1);\n";
+        for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) red_add_s32(&P.rc[xc" << a << "], 1);\n";
     }
     int deaths = 0;
-    for (int d = 0; d < r.ndelta; d++) {
-        const int32_t w = r.delta[d];
-        const int q = w & 0xff, dv = w >> 8;
-        o << "        atomicAdd(&P.rc[reg[" << q << "]], " << dv << ");\n";
-        if (dv < 0) deaths++;
+    std::vector<std::pair<int, int>> deltas;
+    if (rp) {
+        deltas = rp->delta;
+    } else {
+        for (int d = 0; d < r.ndelta; d++) deltas.push_back({r.delta[d] & 0xff, r.delta[d] >> 8});
+    }
+    for (auto &e : deltas) {
+        o << "        red_add_s32(&P.rc[reg[" << e.first << "]], " << e.second << ");\n";
+        if (e.second < 0) deaths++;
     }
     if (deaths) o << "        C.deaths += " << deaths << ";\n";
     if (r.rootvar) {
@@ -254,7 +318,7 @@ void gen_apply_rule(std::ostringstream &o, const Program &P, const RuleView &r)
         o << "        P.hs[i] = " << r.rootval << ";\n";
         std::vector<std::string> ops;
         for (int a = 0; a < r.root_nargs; a++) {
-            ops.push_back(operand(r.build[a]));
+            ops.push_back(opnd(r.build[a]));
             o << "        P.args[" << a << "LL * cap + i] = " << ops.back() << ";\n";
         }
         o << "        if (mode == M_LEARNED) {\n            learned_push(P, i, k + 1, push, npush);\n"
@@ -272,6 +336,21 @@ void gen_apply_rule(std::ostringstream &o, const Program &P, const RuleView &r)
         o << "        }\n";
     }
     if (r.nnew) o << "        C.allocs += " << r.nnew << ";\n";
+}
+
+void gen_apply_rule(std::ostringstream &o, const Program &P, const RuleView &r)
+{
+    o << "    case " << r.slot << ": {  // rule " << r.orig << "\n";
+    const ReusePlan rp = reuse_plan(r);
+    if (rp.cand.empty()) {
+        gen_apply_body(o, P, r, nullptr);
+    } else {
+        o << "      if (reuse) {\n";
+        gen_apply_body(o, P, r, &rp);
+        o << "      } else {\n";
+        gen_apply_body(o, P, r, nullptr);
+        o << "      }\n";
+    }
     o << "        break;\n    }\n";
 }
 
@@ -310,10 +389,21 @@ std::string generate(const Program &P)
          "                                           Carry &last)\n{\n";
     o << "    last.h = 0;\n    if (r == D_MARK) {\n        apply_mark(P, mode, i, pv, k, C, push, npush);\n        return;\n    }\n";
     o << "    const long long cap = P.cap;\n    const int32_t stamp_new = -(int32_t)(k + 1);\n    (void)stamp_new;\n";
-    o << "    switch (r) {\n";
+    o << "    const bool reuse = (r >> 16) & 1;\n    (void)reuse;\n";
+    o << "    switch (r & 0xffff) {\n";
     for (int s = 0; s < (int)P.rule_orig.size(); s++) gen_apply_rule(o, P, rule_view(P, s));
     o << "    default:\n        break;\n    }\n";
-    o << "    if (P.act) P.act[i] = min(P.act[i], (int32_t)k);\n    C.rewrites++;\n}\n\n}  // namespace trs\n";
+    o << "    if (P.act) P.act[i] = min(P.act[i], (int32_t)k);\n    C.rewrites++;\n}\n\n";
+    // slots to allocate for a decision (new nodes not placed in reused slots)
+    o << "__device__ __forceinline__ int spec_new_count(int d)\n{\n    const bool reuse = (d >> 16) & 1;\n"
+         "    switch (d & 0xffff) {\n";
+    for (int s = 0; s < (int)P.rule_orig.size(); s++) {
+        const RuleView r = rule_view(P, s);
+        const ReusePlan rp = reuse_plan(r);
+        if (rp.cand.empty()) o << "    case " << s << ": return " << r.nnew << ";\n";
+        else o << "    case " << s << ": return reuse ? " << r.nnew - (int)rp.cand.size() << " : " << r.nnew << ";\n";
+    }
+    o << "    default: return 0;\n    }\n}\n\n}  // namespace trs\n";
     return o.str();
 }
 
