@@ -374,6 +374,8 @@ def run_case(name, reps):
     t, build, _ = autotune.workloads()[wl]
     flat, offs = build()
     prog = trs.trs_compile(t)
+    if not (kw or {}).get("generic"):
+        prog.specialise()   # the engine the bench times
     pool = trs.Pool(prog, cap)
     kw = kw or autotune_defaults("frontier", wl)
     for _ in range(reps):

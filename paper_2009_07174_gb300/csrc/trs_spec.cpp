@@ -224,12 +224,15 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
         }
         o << "            reg[0] = i;\n";
         for (size_t q = 1; q < ns.size(); q++) o << "            reg[" << q << "] = " << val_name(ns[q].path) << ";\n";
+        // decision word: rule slot | reuse << 16 | slots to allocate << 17
         if (plans[ri].cand.empty()) {
-            o << "            return " << r.slot << ";\n        } while (0);\n";
+            o << "            return " << (r.slot | (r.nnew << 17)) << ";\n        } while (0);\n";
         } else {
             std::string u;
             for (int q : plans[ri].cand) u += std::string(u.empty() ? "" : " && ") + "rc" + std::to_string(ns[q].argpos) + " == 1";
-            o << "            return " << r.slot << " | ((" << u << ") ? 0x10000 : 0);\n        } while (0);\n";
+            const int with = r.slot | 0x10000 | ((r.nnew - (int)plans[ri].cand.size()) << 17);
+            const int without = r.slot | (r.nnew << 17);
+            o << "            return (" << u << ") ? " << with << " : " << without << ";\n        } while (0);\n";
         }
     }
     o << "        return D_MARK;\n    }\n";
@@ -395,15 +398,8 @@ std::string generate(const Program &P)
     o << "    default:\n        break;\n    }\n";
     o << "    if (P.act) P.act[i] = min(P.act[i], (int32_t)k);\n    C.rewrites++;\n}\n\n";
     // slots to allocate for a decision (new nodes not placed in reused slots)
-    o << "__device__ __forceinline__ int spec_new_count(int d)\n{\n    const bool reuse = (d >> 16) & 1;\n"
-         "    switch (d & 0xffff) {\n";
-    for (int s = 0; s < (int)P.rule_orig.size(); s++) {
-        const RuleView r = rule_view(P, s);
-        const ReusePlan rp = reuse_plan(r);
-        if (rp.cand.empty()) o << "    case " << s << ": return " << r.nnew << ";\n";
-        else o << "    case " << s << ": return reuse ? " << r.nnew - (int)rp.cand.size() << " : " << r.nnew << ";\n";
-    }
-    o << "    default: return 0;\n    }\n}\n\n}  // namespace trs\n";
+    o << "__device__ __forceinline__ int spec_new_count(int d)\n{\n    return (d >> 17) & 0xff;\n}\n\n"
+         "}  // namespace trs\n";
     return o.str();
 }
 
