@@ -355,13 +355,15 @@ PROFILE_CASES = {
     "arith-frontier": ("arith", 1 << 26, None),
     "ttree-frontier": ("ttree", 1 << 24, None),
     # a store already in normal form: the plain sweep is one streaming scan
-    "arith-plain-scan": ("arith-768", 1 << 26, {"mode": "plain"}),
+    # (table-driven, so that the store it scans, built without slot reuse, is
+    # larger than L2)
+    "arith-plain-scan": ("arith-768", 1 << 26, {"mode": "plain", "generic": 1}),
     # the full-size batches (pool 2^28, about 7 GB): single-pass counters only
     "arith-4096-frontier": ("arith-4096", 1 << 28, {"mode": "frontier", "eager": 256, "solo_max": 512}),
     "fib-batch-10000-frontier": ("fib-batch-10000", 1 << 28, {"mode": "frontier", "eager": 64,
                                                               "block_size": 256}),
 }
-PRE_NORMALISE = {"arith-plain-scan": {"mode": "frontier", "eager": 64}}
+PRE_NORMALISE = {"arith-plain-scan": {"mode": "frontier", "eager": 64, "generic": 1}}
 
 
 def run_case(name, reps):
