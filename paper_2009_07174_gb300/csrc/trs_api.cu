@@ -59,7 +59,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t hs, args, rc, nfs, par, pend, ring, fq0, fq1, act, trace, ctl, tab, total;
+    size_t rec, nfs, ring, fq0, fq1, act, trace, ctl, tab, total;
 };
 
 Layout layout(const Program &p, int64_t cap)
@@ -68,12 +68,8 @@ Layout layout(const Program &p, int64_t cap)
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes); return at; };
     const size_t slots = (size_t)cap * sizeof(int32_t);
-    L.hs = take(slots);
-    L.args = take(slots * (size_t)std::max(1, p.maxarity));
-    L.rc = take(slots);
+    L.rec = take(slots * (size_t)rec_stride(p.maxarity));
     L.nfs = take(slots);
-    L.par = take(slots);
-    L.pend = take(slots);
     L.ring = take(slots);
     L.fq0 = take(slots);
     L.fq1 = take(slots);
@@ -171,12 +167,9 @@ int trs_pool_create(const trs_program *prog, int64_t capacity, void *dev_mem, si
     pool->bytes = bytes;
     char *b = (char *)dev_mem;
     DevPool &d = pool->d;
-    d.hs = (int32_t *)(b + L.hs);
-    d.args = (int32_t *)(b + L.args);
-    d.rc = (int32_t *)(b + L.rc);
+    d.rec = (int32_t *)(b + L.rec);
+    d.rs = rec_stride(p.maxarity);
     d.nfs = (int32_t *)(b + L.nfs);
-    d.par = (int32_t *)(b + L.par);
-    d.pend = (int32_t *)(b + L.pend);
     d.ring = (int32_t *)(b + L.ring);
     d.fq[0] = (int32_t *)(b + L.fq0);
     d.fq[1] = (int32_t *)(b + L.fq1);
@@ -244,9 +237,10 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
         set_error("term_upload_batch: pool full");
         return TRS_ERR_POOL_FULL;
     }
-    const int ma = std::max(1, p.maxarity);
-    std::vector<int32_t> hs(total), rc(total, 1), nfs(total, -(int32_t)h.sweep_id), par(total, 0);
-    std::vector<int32_t> args((size_t)ma * total, 0);
+    const int ma = p.maxarity, rs = rec_stride(ma);
+    // records: head, arguments, parent word, count 1 (the tree edge or the
+    // root's pin), pending 0 (set by the seed scan)
+    std::vector<int32_t> rec((size_t)rs * total, 0), nfs(total, -(int32_t)h.sweep_id);
     struct Open { int64_t node; int32_t next, arity; };
     std::vector<Open> stk;
     for (int32_t t = 0; t < nterms; t++) {
@@ -256,12 +250,14 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
         for (int64_t q = 0; q < len; q++) {
             const int32_t s = flat[offsets[t] + q];
             const int64_t node = b + q;
-            hs[node] = s;
+            int32_t *r = &rec[(size_t)node * rs];
+            r[kRecHead] = s;
+            r[rec_rc(ma)] = 1;
             if (!stk.empty()) {
                 Open &o = stk.back();
-                args[(size_t)o.next * total + o.node] = (int32_t)(base + node);
+                rec[(size_t)o.node * rs + rec_arg(o.next)] = (int32_t)(base + node);
                 // sign bit: the parent's head is unary (its only argument)
-                par[node] = (int32_t)((uint32_t)(base + o.node) | (o.arity == 1 ? 0x80000000u : 0u));
+                r[rec_par(ma)] = (int32_t)((uint32_t)(base + o.node) | (o.arity == 1 ? 0x80000000u : 0u));
                 if (++o.next == o.arity) stk.pop_back();
             }
             if (p.arity[s] > 0) stk.push_back({node, 0, p.arity[s]});
@@ -270,13 +266,9 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
     }
     const size_t sz = (size_t)total * sizeof(int32_t);
     const DevPool &d = pool->d;
-    CK(cudaMemcpyAsync(d.hs + base, hs.data(), sz, cudaMemcpyHostToDevice, stream), "upload hs");
-    for (int j = 0; j < p.maxarity; j++)
-        CK(cudaMemcpyAsync(d.args + (size_t)j * d.cap + base, args.data() + (size_t)j * total, sz,
-                           cudaMemcpyHostToDevice, stream), "upload args");
-    CK(cudaMemcpyAsync(d.rc + base, rc.data(), sz, cudaMemcpyHostToDevice, stream), "upload rc");
+    CK(cudaMemcpyAsync(d.rec + (size_t)base * rs, rec.data(), sz * rs, cudaMemcpyHostToDevice, stream),
+       "upload records");
     CK(cudaMemcpyAsync(d.nfs + base, nfs.data(), sz, cudaMemcpyHostToDevice, stream), "upload nfs");
-    CK(cudaMemcpyAsync(d.par + base, par.data(), sz, cudaMemcpyHostToDevice, stream), "upload par");
     long long ntop = base + total;
     CK(cudaMemcpyAsync(&d.ctl->n_top, &ntop, sizeof(ntop), cudaMemcpyHostToDevice, stream), "upload n_top");
     CK(cudaStreamSynchronize(stream), "upload synchronize");
@@ -536,16 +528,15 @@ int term_download_batch(trs_pool *pool, const int32_t *roots, int32_t nroots, in
         if (roots[r] <= 0 || roots[r] >= n) { set_error("term_download: root out of range"); return TRS_ERR_STATE; }
         int32_t v[2];
         CK(cudaMemcpyAsync(&v[0], d.nfs + roots[r], sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "read root");
-        CK(cudaMemcpyAsync(&v[1], d.rc + roots[r], sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "read root");
+        CK(cudaMemcpyAsync(&v[1], d.rec + (size_t)roots[r] * d.rs + rec_rc(p.maxarity), sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, stream), "read root");
         CK(cudaStreamSynchronize(stream), "read root");
         if (v[0] == 0 || v[1] <= 0) { set_error("term_download: root is not live"); return TRS_ERR_STATE; }
     }
-    std::vector<int32_t> hs(n);
-    std::vector<int32_t> args((size_t)std::max(1, p.maxarity) * n);
-    CK(cudaMemcpyAsync(hs.data(), d.hs, n * sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "download hs");
-    for (int j = 0; j < p.maxarity; j++)
-        CK(cudaMemcpyAsync(args.data() + (size_t)j * n, d.args + (size_t)j * d.cap, n * sizeof(int32_t),
-                           cudaMemcpyDeviceToHost, stream), "download args");
+    const int rs = d.rs;
+    std::vector<int32_t> rec((size_t)n * rs);
+    CK(cudaMemcpyAsync(rec.data(), d.rec, (size_t)n * rs * sizeof(int32_t), cudaMemcpyDeviceToHost, stream),
+       "download records");
     CK(cudaStreamSynchronize(stream), "download synchronize");
     int64_t out = 0;
     std::vector<int32_t> stk;
@@ -557,11 +548,12 @@ int term_download_batch(trs_pool *pool, const int32_t *roots, int32_t nroots, in
             int32_t x = stk.back();
             stk.pop_back();
             if (x <= 0 || x >= n) { set_error("term_download: dangling index"); return TRS_ERR_STATE; }
-            int32_t s = hs[x];
+            const int32_t *r = &rec[(size_t)x * rs];
+            int32_t s = r[kRecHead];
             if (s <= 0 || s >= p.nsym) { set_error("term_download: corrupt node"); return TRS_ERR_STATE; }
             if (out < cap) buf[out] = s;
             out++;
-            for (int a = p.arity[s] - 1; a >= 0; a--) stk.push_back(args[(size_t)a * n + x]);
+            for (int a = p.arity[s] - 1; a >= 0; a--) stk.push_back(r[rec_arg(a)]);
         }
         offsets_out[r + 1] = out;
     }

@@ -208,9 +208,10 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
     if (carried) {
         h = cin.h;
     } else {
-        h = P.hs[i];
-        if (P.ma > 0) w0 = P.args[i];
-        if (P.ma > 1) w1 = P.args[cap + i];
+        const int4 q = rec_head4(P, i);
+        h = q.x;
+        w0 = q.y;
+        w1 = q.z;
     }
     h_out = h;
     const int aw = T.w[T.off_ar + h];
@@ -225,7 +226,7 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
             c[j] = (carried && j < kCarryArgs) ? cin.c[j]
                    : j == 0                    ? w0
                    : j == 1                    ? w1
-                                               : P.args[j * cap + i];
+                                               : arg_at(P, j, i);
     }
     if (check_ready) {
         bool ready = true;
@@ -240,17 +241,21 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
     for (int a = 0; a < kPf; a++) {
         hc[a] = d0[a] = d1[a] = e0[a] = e1[a] = 0;
         if (a < ar) {
-            if ((plan >> (16 + a)) & 1) hc[a] = P.hs[c[a]];
-            if ((plan >> a) & 1) d0[a] = P.args[c[a]];
-            if ((plan >> (4 + a)) & 1) d1[a] = P.args[cap + c[a]];
+            if (((plan >> (16 + a)) | (plan >> a) | (plan >> (4 + a))) & 1) {
+                // head and first two argument words of the argument together
+                const int4 q = rec_head4(P, c[a]);
+                hc[a] = q.x;
+                d0[a] = q.y;
+                d1[a] = q.z;
+            }
         }
     }
 #pragma unroll
     for (int a = 0; a < kPf; a++) {
         d0[a] = in_store(d0[a], cap);
         d1[a] = in_store(d1[a], cap);
-        if ((plan >> (8 + a)) & 1) e0[a] = P.hs[d0[a]];
-        if ((plan >> (12 + a)) & 1) e1[a] = P.hs[d1[a]];
+        if ((plan >> (8 + a)) & 1) e0[a] = hs_at(P, d0[a]);
+        if ((plan >> (12 + a)) & 1) e1[a] = hs_at(P, d1[a]);
     }
     for (int r = r0; r < r1; r++) {
         const int32_t *R = T.rule(r);
@@ -283,12 +288,12 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
                     node = pick(d1, a);
                     if ((plan >> (12 + a)) & 1) { hn = pick(e1, a); have = true; }
                 } else {
-                    node = P.args[(long long)ap * cap + reg[pr]];
+                    node = arg_at(P, ap, reg[pr]);
                 }
             }
             reg[q] = node;
             if (sym != 0) {
-                if (!have) hn = P.hs[node];
+                if (!have) hn = hs_at(P, node);
                 if (hn != sym) { ok = false; break; }
             }
         }
@@ -461,7 +466,7 @@ __device__ __forceinline__ void notify_parent(const DevPool &P, int32_t pv, int3
 {
     const int32_t p = pv & 0x7fffffff;
     if (p == 0) return;
-    if (pv < 0 || atom_acqrel_add_s32(&P.pend[p], -1) == 1) push[npush++] = p;
+    if (pv < 0 || atom_acqrel_add_s32(&pend_at(P, p), -1) == 1) push[npush++] = p;
 }
 
 // Learned frontier: every node enters the next frontier at most once per
@@ -469,7 +474,7 @@ __device__ __forceinline__ void notify_parent(const DevPool &P, int32_t pv, int3
 __device__ __forceinline__ void learned_push(const DevPool &P, int32_t x, long long k_next, int32_t *push,
                                              int &npush)
 {
-    if (atomicExch(&P.pend[x], (int32_t)k_next) != (int32_t)k_next) push[npush++] = x;
+    if (atomicExch(&pend_at(P, x), (int32_t)k_next) != (int32_t)k_next) push[npush++] = x;
 }
 
 __device__ __forceinline__ int32_t par_word(const Tab &T, int32_t parent, int32_t parent_sym)
@@ -534,24 +539,24 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         int32_t sym = w0 & 0xffff, na = w0 >> 16;
         int32_t parent = (w1 & 0xffff) - 1, pj = w1 >> 16;
         int32_t x = nw[j];
-        P.hs[x] = sym;
+        hs_at(P, x) = sym;
         Carry cx;
         cx.h = na <= kCarryArgs ? sym : 0;
         for (int a = 0; a < na; a++) {
             int32_t op = build[pos++];
             const int32_t v = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
-            P.args[a * cap + x] = v;
+            arg_at(P, a, x) = v;
             if (a < kCarryArgs) cx.c[a] = v;
         }
-        P.rc[x] = 1;
+        rc_at(P, x) = 1;
         P.nfs[x] = stamp_new;
-        P.par[x] = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
+        par_at(P, x) = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
         if (mode == M_LEARNED) {
-            P.pend[x] = (int32_t)(k + 1);
+            pend_at(P, x) = (int32_t)(k + 1);
             push[npush++] = x;
             last.h = 0;
         } else {
-            P.pend[x] = pj;
+            pend_at(P, x) = pj;
             if (mode == M_FRONTIER && pj == 0) {
                 push[npush++] = x;
                 last = cx;
@@ -563,16 +568,14 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     int32_t xc[TRS_MAX_ARITY];
     if (rootvar) {
         int32_t x = reg[R[1]];
-        xh = P.hs[x];
-        // the first two argument words are read with the head (before the
-        // arity is known); words beyond the arity are not used
-        int32_t sp0 = 0, sp1 = 0;
-        if (P.ma > 0) sp0 = P.args[x];
-        if (P.ma > 1) sp1 = P.args[cap + x];
+        // the first argument words are read with the head (before the arity
+        // is known); words beyond the arity are not used
+        const int4 q = rec_head4(P, x);
+        xh = q.x;
         xa = T.arity(xh);
         for (int a = 0; a < xa; a++) {
-            xc[a] = a == 0 ? sp0 : a == 1 ? sp1 : P.args[a * cap + x];
-            red_add_s32(&P.rc[xc[a]], 1);
+            xc[a] = a < 3 ? quad_word(q, 1 + a) : arg_at(P, a, x);
+            red_add_s32(&rc_at(P, xc[a]), 1);
         }
     }
     // net reference changes of matched nodes, positive ones first; fire and
@@ -582,12 +585,12 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     for (int d = 0; d < ndelta; d++) {
         int32_t w = delta[d];
         int32_t q = w & 0xff, dv = w >> 8;
-        red_add_s32(&P.rc[reg[q]], dv);
+        red_add_s32(&rc_at(P, reg[q]), dv);
         if (dv < 0) C.deaths++;
     }
     if (rootvar) {
-        P.hs[i] = xh;
-        for (int a = 0; a < xa; a++) P.args[a * cap + i] = xc[a];
+        hs_at(P, i) = xh;
+        for (int a = 0; a < xa; a++) arg_at(P, a, i) = xc[a];
         P.nfs[i] = (int32_t)(k + 1);
         const int before = npush;
         if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
@@ -597,20 +600,20 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         }
         if (npush != before) last.h = 0;
     } else {
-        P.hs[i] = R[1];
+        hs_at(P, i) = R[1];
         Carry ci;
         ci.h = root_nargs <= kCarryArgs ? R[1] : 0;
         for (int a = 0; a < root_nargs; a++) {
             int32_t op = build[a];
             const int32_t v = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
-            P.args[a * cap + i] = v;
+            arg_at(P, a, i) = v;
             if (a < kCarryArgs) ci.c[a] = v;
         }
         if (mode == M_LEARNED) {
             learned_push(P, i, k + 1, push, npush);
             last.h = 0;
         } else {
-            P.pend[i] = root_pend;
+            pend_at(P, i) = root_pend;
             if (mode == M_FRONTIER && root_pend == 0) {
                 push[npush++] = i;
                 last = ci;
@@ -679,7 +682,7 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     if (keep) learned_push(P, i, S.k + 1, push, npush);  // learned: not yet eligible, keep it
     // the parent word is loaded together with the node (it is needed when the
     // node turns out to be a normal form), not after the decision
-    const int32_t pv = (mode != M_PLAIN && cand) ? P.par[i] : 0;
+    const int32_t pv = (mode != M_PLAIN && cand) ? par_at(P, i) : 0;
     if (cand) {
         C.visits++;
 #ifdef TRS_JIT
@@ -958,7 +961,7 @@ __device__ __forceinline__ void phase_gc(const DevPool &P, const Tab &T, const S
         int nfreed = 0;
         for (int t = 0; t < kGcPer; t++) {
             const long long i = base + t;
-            if (i < 1 || sv[t] == 0 || P.rc[i] != 0) continue;
+            if (i < 1 || sv[t] == 0 || rc_at(P, i) != 0) continue;
             if (atomicExch(&P.nfs[i], 0) == 0) continue;
             // claimed: free it and follow the nodes it kills, keeping room for
             // this thread's remaining slots
@@ -969,10 +972,10 @@ __device__ __forceinline__ void phase_gc(const DevPool &P, const Tab &T, const S
             while (sp > 0) {
                 const int32_t x = stk[--sp];
                 freed[nfreed++] = x;
-                const int ar = T.arity(P.hs[x]);
+                const int ar = T.arity(hs_at(P, x));
                 for (int a = 0; a < ar; a++) {
-                    const int32_t c = P.args[a * P.cap + x];
-                    if (atomicSub(&P.rc[c], 1) == 1) {
+                    const int32_t c = arg_at(P, a, x);
+                    if (atomicSub(&rc_at(P, c), 1) == 1) {
                         if (nfreed + sp < room) {
                             if (atomicExch(&P.nfs[c], 0) != 0) stk[sp++] = c;
                         } else {
@@ -1033,13 +1036,13 @@ __device__ __forceinline__ void phase_seed(const DevPool &P, const Tab &T, const
         for (int t = 0; t < 4; t++) {
             const long long i = base + t;
             if (i < 1 || sv[t] >= 0) continue;
-            const int ar = T.arity(P.hs[i]);
+            const int ar = T.arity(hs_at(P, i));
             int cnt = 0;
             for (int a = 0; a < ar; a++) {
-                const int32_t c = P.args[a * P.cap + i];
+                const int32_t c = arg_at(P, a, i);
                 if (!is_nf_at(P.nfs[c], S.k)) cnt++;
             }
-            P.pend[i] = cnt;
+            pend_at(P, i) = cnt;
             if (cnt == 0 && -(long long)sv[t] <= S.k) ready[nready++] = (int32_t)i;
         }
         int total = 0;
@@ -1065,15 +1068,15 @@ namespace trs {
 __device__ __forceinline__ void node_features(const DevPool &P, const Tab &T, int32_t i, long long k,
                                               int &h, int32_t *a, unsigned &bits)
 {
-    h = P.hs[i];
+    h = hs_at(P, i);
     const int ar = T.arity(h);
     bits = 0;
 #pragma unroll
     for (int j = 0; j < TRS_MAX_ARITY; j++) {
         a[j] = 0;
         if (j < P.ma && j < ar) {
-            const int32_t c = P.args[j * P.cap + i];
-            a[j] = P.hs[c];
+            const int32_t c = arg_at(P, j, i);
+            a[j] = hs_at(P, c);
             if (is_nf_at(P.nfs[c], k)) bits |= 1u << j;
         }
     }

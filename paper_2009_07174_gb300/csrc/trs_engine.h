@@ -112,14 +112,24 @@ struct Ctl {
     Acc acc[3];
 };
 
+// Node records.  Slot x occupies rec[x * rs, (x + 1) * rs): its head symbol,
+// its ma argument indices, its parent word (frontier modes: the parent of a
+// node not in normal form, sign bit set when that parent is unary), its
+// reference count and its number of arguments not yet in normal form, then
+// padding.  A record is one 32-byte sector up to arity 4 (64 bytes above),
+// so one node costs one sector however many of its fields a step touches.
+// The normal-form stamps stay a separate array for the streaming scans.
+TRS_HD inline int rec_stride(int ma) { return ma + 4 <= 8 ? 8 : 16; }
+constexpr int kRecHead = 0;
+TRS_HD inline int rec_arg(int a) { return 1 + a; }
+TRS_HD inline int rec_par(int ma) { return 1 + ma; }
+TRS_HD inline int rec_rc(int ma) { return 2 + ma; }
+TRS_HD inline int rec_pend(int ma) { return 3 + ma; }
+
 struct DevPool {
-    int32_t *hs;    // head symbol per slot
-    int32_t *args;  // args[j * cap + i]
-    int32_t *rc;    // reference counts
+    int32_t *rec;   // node records, rs words per slot
     int32_t *nfs;   // >0: in normal form from sweep nfs; <0: not, eligible from
                     // sweep -nfs; 0: free slot
-    int32_t *par;   // frontier mode: the parent of a node not in normal form
-    int32_t *pend;  // frontier mode: arguments not yet in normal form
     int32_t *ring;  // free ring, cap entries, position p at ring[p % cap]
     int32_t *fq[2]; // frontier buffers
     int32_t *act;   // predictor traces: first sweep a node acted after a sample
@@ -128,6 +138,7 @@ struct DevPool {
     const int32_t *tab;  // compiled rule table
     long long cap;
     int32_t ma;
+    int32_t rs;     // record stride in words (rec_stride(ma))
     int32_t tab_words;
     int32_t trace_cap;
     int32_t nsym;
@@ -139,6 +150,44 @@ struct DevPool {
     float *samp_label;
     long long samp_cap;
 };
+
+#ifdef __CUDACC__
+// ---------------------------------------------------------------------------
+// node record accessors (layout above).  The specialised engine compiles
+// with the stride and arity as constants.
+__device__ __forceinline__ int rec_rs(const DevPool &P)
+{
+#ifdef TRS_JIT_RS
+    return TRS_JIT_RS;
+#else
+    return P.rs;
+#endif
+}
+__device__ __forceinline__ int rec_ma(const DevPool &P)
+{
+#ifdef TRS_JIT_MA
+    return TRS_JIT_MA;
+#else
+    return P.ma;
+#endif
+}
+__device__ __forceinline__ int32_t *node_at(const DevPool &P, long long x) { return P.rec + x * rec_rs(P); }
+__device__ __forceinline__ int32_t &hs_at(const DevPool &P, long long x) { return node_at(P, x)[kRecHead]; }
+__device__ __forceinline__ int32_t &arg_at(const DevPool &P, int a, long long x) { return node_at(P, x)[rec_arg(a)]; }
+__device__ __forceinline__ int32_t &par_at(const DevPool &P, long long x) { return node_at(P, x)[rec_par(rec_ma(P))]; }
+__device__ __forceinline__ int32_t &rc_at(const DevPool &P, long long x) { return node_at(P, x)[rec_rc(rec_ma(P))]; }
+__device__ __forceinline__ int32_t &pend_at(const DevPool &P, long long x) { return node_at(P, x)[rec_pend(rec_ma(P))]; }
+// the first four words of a record (head, arguments, ...) in one load
+__device__ __forceinline__ int4 rec_head4(const DevPool &P, long long x)
+{
+    return *reinterpret_cast<const int4 *>(node_at(P, x));
+}
+// word w (< 4) of a loaded head quadruple
+__device__ __forceinline__ int32_t quad_word(const int4 &q, int w)
+{
+    return w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+}
+#endif
 
 constexpr int kTraceCap = 65536;
 

@@ -18,7 +18,7 @@ namespace trs {
 // Unpin a root (term_release).
 __global__ void k_release(DevPool P, int32_t root)
 {
-    if (atomicSub(&P.rc[root], 1) == 1) atomicAdd((unsigned long long *)&P.ctl->dead, 1ull);
+    if (atomicSub(&rc_at(P, root), 1) == 1) atomicAdd((unsigned long long *)&P.ctl->dead, 1ull);
 }
 
 // Slot 0 is the null node: never live, never free-listed.
@@ -27,11 +27,8 @@ __global__ void k_reset(DevPool P)
     Ctl *c = P.ctl;
     c->sweep_id = 1;
     c->n_top = 1;
-    P.hs[0] = 0;
+    for (int w = 0; w < P.rs; w++) P.rec[w] = 0;
     P.nfs[0] = 0;
-    P.rc[0] = 0;
-    P.par[0] = 0;
-    P.pend[0] = 0;
 }
 
 // ---------------------------------------------------------------------------

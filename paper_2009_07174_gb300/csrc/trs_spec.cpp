@@ -162,7 +162,7 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
     o << "    case " << h << ": {\n";
     for (int j = 0; j < ar; j++) {
         if (j < 4) o << "        const int32_t c" << j << " = w" << j << ";\n";
-        else o << "        const int32_t c" << j << " = P.args[" << j << "LL * cap + i];\n";
+        else o << "        const int32_t c" << j << " = arg_at(P, " << j << ", i);\n";
     }
     if (ar > 0) {
         o << "        if (check_ready) {\n            bool ready = true;\n";
@@ -190,12 +190,22 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
         plans.push_back(reuse_plan(rules[ri]));
         for (int q : plans.back().cand) rcpos.insert(nodes[ri][q].argpos);
     }
-    // level 1: argument heads and second-level words together
-    for (auto &p : sym1) o << "        const int32_t " << sym_name(p) << " = P.hs[" << val_name(p) << "];\n";
-    for (int j : rcpos) o << "        const int32_t rc" << j << " = P.rc[c" << j << "];\n";
+    // level 1: argument heads and second-level words together, one load of
+    // the first four record words per argument (the count is in the same
+    // sector)
+    std::set<int> quad;
+    for (auto &p : sym1) quad.insert(p[0]);
     for (auto &p : val2)
-        o << "        const int32_t " << val_name(p) << " = in_store(P.args[" << p[1] << "LL * cap + c" << p[0]
-          << "], cap);\n";
+        if (p[1] < 3) quad.insert(p[0]);
+    for (int j : quad) o << "        const int4 n" << j << " = rec_head4(P, c" << j << ");\n";
+    for (int j : rcpos) o << "        const int32_t rc" << j << " = rc_at(P, c" << j << ");\n";
+    for (auto &p : sym1) o << "        const int32_t " << sym_name(p) << " = n" << p[0] << ".x;\n";
+    for (auto &p : val2) {
+        if (p[1] < 3)
+            o << "        const int32_t " << val_name(p) << " = in_store(n" << p[0] << "." << "yzw"[p[1]] << ", cap);\n";
+        else
+            o << "        const int32_t " << val_name(p) << " = in_store(arg_at(P, " << p[1] << ", c" << p[0] << "), cap);\n";
+    }
     std::set<std::vector<int>> emitted;
     for (size_t ri = 0; ri < rules.size(); ri++) {
         const RuleView &r = rules[ri];
@@ -204,7 +214,7 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
         for (size_t q = 1; q < ns.size(); q++)
             if (ns[q].path.size() == 2 && ns[q].sym && !emitted.count(ns[q].path)) {
                 emitted.insert(ns[q].path);
-                o << "        const int32_t " << sym_name(ns[q].path) << " = P.hs[" << val_name(ns[q].path) << "];\n";
+                o << "        const int32_t " << sym_name(ns[q].path) << " = hs_at(P, " << val_name(ns[q].path) << ");\n";
             }
         o << "        do {  // rule " << r.orig << "\n";
         std::string cond;
@@ -218,9 +228,9 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
             const PatNode &n = ns[q];
             if (n.path.size() <= 2) continue;
             std::vector<int> pp(n.path.begin(), n.path.end() - 1);
-            o << "            const int32_t " << val_name(n.path) << " = P.args[" << n.argpos << "LL * cap + "
-              << val_name(pp) << "];\n";
-            if (n.sym) o << "            if (P.hs[" << val_name(n.path) << "] != " << n.sym << ") break;\n";
+            o << "            const int32_t " << val_name(n.path) << " = arg_at(P, " << n.argpos << ", "
+              << val_name(pp) << ");\n";
+            if (n.sym) o << "            if (hs_at(P, " << val_name(n.path) << ") != " << n.sym << ") break;\n";
         }
         o << "            reg[0] = i;\n";
         for (size_t q = 1; q < ns.size(); q++) o << "            reg[" << q << "] = " << val_name(ns[q].path) << ";\n";
@@ -261,23 +271,31 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
             o << "        {\n            const int32_t x = reg[" << rp->cand[j] << "];\n";
         else
             o << "        {\n            const int32_t x = nw[" << j - npairs << "];\n";
-        o << "            P.hs[x] = " << sym << ";\n";
         std::vector<std::string> ops;
-        for (int a = 0; a < na; a++) {
-            ops.push_back(opnd(r.build[pos++]));
-            o << "            P.args[" << a << "LL * cap + x] = " << ops.back() << ";\n";
-        }
-        o << "            P.rc[x] = 1;\n            P.nfs[x] = stamp_new;\n";
+        for (int a = 0; a < na; a++) ops.push_back(opnd(r.build[pos++]));
+        std::string parw;
         if (parent < 0) {
             const bool un = arity_of(P, r.rootval) == 1;
-            o << "            P.par[x] = i" << (un ? " | (int32_t)0x80000000" : "") << ";\n";
+            parw = std::string("i") + (un ? " | (int32_t)0x80000000" : "");
         } else {
             const bool un = arity_of(P, new_sym[parent]) == 1;
-            o << "            P.par[x] = " << new_slot(parent) << (un ? " | (int32_t)0x80000000" : "") << ";\n";
+            parw = new_slot(parent) + (un ? " | (int32_t)0x80000000" : "");
         }
-        o << "            if (mode == M_LEARNED) {\n                P.pend[x] = (int32_t)(k + 1);\n"
-             "                push[npush++] = x;\n                last.h = 0;\n            } else {\n";
-        o << "                P.pend[x] = " << pj << ";\n";
+        // the whole record in 16-byte stores: head, arguments, parent word,
+        // count 1, pending arguments (learned mode: the sweep it was queued for)
+        const int ma = P.maxarity, rs = rec_stride(ma);
+        std::vector<std::string> w(rs, "0");
+        w[kRecHead] = std::to_string(sym);
+        for (int a = 0; a < na; a++) w[rec_arg(a)] = ops[a];
+        w[rec_par(ma)] = "(" + parw + ")";
+        w[rec_rc(ma)] = "1";
+        w[rec_pend(ma)] = "(mode == M_LEARNED ? (int32_t)(k + 1) : " + std::to_string(pj) + ")";
+        for (int q = 0; q < rs; q += 4)
+            o << "            reinterpret_cast<int4 *>(node_at(P, x))[" << q / 4 << "] = make_int4(" << w[q] << ", "
+              << w[q + 1] << ", " << w[q + 2] << ", " << w[q + 3] << ");\n";
+        o << "            P.nfs[x] = stamp_new;\n";
+        o << "            if (mode == M_LEARNED) {\n                push[npush++] = x;\n                last.h = 0;\n"
+             "            } else {\n";
         if (pj == 0) {
             o << "                if (mode == M_FRONTIER) {\n                    push[npush++] = x;\n";
             if (na <= 4) {
@@ -292,10 +310,14 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
     }
     const int ma = P.maxarity;
     if (r.rootvar) {
-        o << "        const int32_t x = reg[" << r.rootval << "];\n        const int32_t xh = P.hs[x];\n";
-        for (int a = 0; a < ma; a++) o << "        int32_t xc" << a << " = P.args[" << a << "LL * cap + x];\n";
+        o << "        const int32_t x = reg[" << r.rootval << "];\n        const int4 xq = rec_head4(P, x);\n"
+             "        const int32_t xh = xq.x;\n";
+        for (int a = 0; a < ma; a++) {
+            if (a < 3) o << "        const int32_t xc" << a << " = xq." << "yzw"[a] << ";\n";
+            else o << "        const int32_t xc" << a << " = arg_at(P, " << a << ", x);\n";
+        }
         o << "        const int xa = T.arity(xh);\n";
-        for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) red_add_s32(&P.rc[xc" << a << "], 1);\n";
+        for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) red_add_s32(&rc_at(P, xc" << a << "), 1);\n";
     }
     int deaths = 0;
     std::vector<std::pair<int, int>> deltas;
@@ -305,27 +327,27 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
         for (int d = 0; d < r.ndelta; d++) deltas.push_back({r.delta[d] & 0xff, r.delta[d] >> 8});
     }
     for (auto &e : deltas) {
-        o << "        red_add_s32(&P.rc[reg[" << e.first << "]], " << e.second << ");\n";
+        o << "        red_add_s32(&rc_at(P, reg[" << e.first << "]), " << e.second << ");\n";
         if (e.second < 0) deaths++;
     }
     if (deaths) o << "        C.deaths += " << deaths << ";\n";
     if (r.rootvar) {
-        o << "        P.hs[i] = xh;\n";
-        for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) P.args[" << a << "LL * cap + i] = xc" << a << ";\n";
+        o << "        hs_at(P, i) = xh;\n";
+        for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) arg_at(P, " << a << ", i) = xc" << a << ";\n";
         o << "        P.nfs[i] = (int32_t)(k + 1);\n        {\n            const int before = npush;\n"
              "            if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);\n"
              "            if (mode == M_LEARNED) {\n                const int32_t p = pv & 0x7fffffff;\n"
              "                if (p != 0) learned_push(P, p, k + 1, push, npush);\n            }\n"
              "            if (npush != before) last.h = 0;\n        }\n";
     } else {
-        o << "        P.hs[i] = " << r.rootval << ";\n";
+        o << "        hs_at(P, i) = " << r.rootval << ";\n";
         std::vector<std::string> ops;
         for (int a = 0; a < r.root_nargs; a++) {
             ops.push_back(opnd(r.build[a]));
-            o << "        P.args[" << a << "LL * cap + i] = " << ops.back() << ";\n";
+            o << "        arg_at(P, " << a << ", i) = " << ops.back() << ";\n";
         }
         o << "        if (mode == M_LEARNED) {\n            learned_push(P, i, k + 1, push, npush);\n"
-             "            last.h = 0;\n        } else {\n            P.pend[i] = " << r.root_pend << ";\n";
+             "            last.h = 0;\n        } else {\n            pend_at(P, i) = " << r.root_pend << ";\n";
         if (r.root_pend == 0) {
             o << "            if (mode == M_FRONTIER) {\n                push[npush++] = i;\n";
             if (r.root_nargs <= 4) {
@@ -372,8 +394,11 @@ std::string generate(const Program &P)
     for (int j = 0; j < 4; j++) o << "    int32_t w" << j << " = 0;\n";
     o << "    if (cin.h != 0) {\n        h = cin.h;\n";
     for (int j = 0; j < mw; j++) o << "        w" << j << " = cin.c[" << j << "];\n";
-    o << "    } else {\n        h = P.hs[i];\n";
-    for (int j = 0; j < mw; j++) o << "        w" << j << " = P.args[" << j << "LL * cap + i];\n";
+    o << "    } else {\n        const int4 q = rec_head4(P, i);\n        h = q.x;\n";
+    for (int j = 0; j < mw; j++) {
+        if (j < 3) o << "        w" << j << " = q." << "yzw"[j] << ";\n";
+        else o << "        w" << j << " = arg_at(P, " << j << ", i);\n";
+    }
     o << "    }\n    h_out = h;\n    switch (h) {\n";
     for (int h = 1; h < P.nsym; h++)
         if (first[h + 1] > first[h]) gen_decide_head(o, P, h, first[h], first[h + 1]);
@@ -381,7 +406,7 @@ std::string generate(const Program &P)
     // heads without rules: a normal form once the arguments are
     o << "    if (check_ready) {\n        const int ar = T.arity(h);\n        bool ready = true;\n";
     for (int j = 0; j < P.maxarity; j++) {
-        const std::string w = j < 4 ? "w" + std::to_string(j) : "P.args[" + std::to_string(j) + "LL * cap + i]";
+        const std::string w = j < 4 ? "w" + std::to_string(j) : "arg_at(P, " + std::to_string(j) + ", i)";
         o << "        if (" << j << " < ar) ready &= is_nf_at(P.nfs[" << w << "], k);\n";
     }
     o << "        if (!ready) return D_SKIP;\n    }\n    return D_MARK;\n}\n\n";
@@ -527,8 +552,9 @@ int compile_spec(const trs_program *prog, int cc, const char *cache_dir, std::ve
 {
     const std::string arch = "--gpu-architecture=sm_" + std::to_string(cc) + "a";
     gen = generate(prog->p);
-    const std::string src =
-        "#define TRS_JIT 1\n#include \"trs_device.cuh\"\n" + gen + "#include \"trs_engine_kernel.cuh\"\n";
+    const std::string src = "#define TRS_JIT 1\n#define TRS_JIT_MA " + std::to_string(prog->p.maxarity) +
+                            "\n#define TRS_JIT_RS " + std::to_string(rec_stride(prog->p.maxarity)) +
+                            "\n#include \"trs_device.cuh\"\n" + gen + "#include \"trs_engine_kernel.cuh\"\n";
     const std::string inc = "-I" + cuda_include_dir();
     std::vector<std::string> opts = {arch, "-std=c++17", "-default-device", inc, "--ptxas-options=-v"};
     // cache key: generated code, engine sources, options

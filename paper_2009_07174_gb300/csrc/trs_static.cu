@@ -54,19 +54,16 @@ long long carve(unsigned char *base, const Program &p, DevPool *d)
     d->tab = (const int32_t *)(base + off);
     d->tab_words = (int32_t)p.table.size();
     off = up(off + p.table.size() * sizeof(int32_t));
-    const int ma = std::max(1, p.maxarity);
-    const int arrays = 9 + ma;  // hs, args[ma], rc, nfs, par, pend, ring, fq0, fq1, stack
-    if (off + (size_t)arrays * 256 >= kStaticBytes) return 0;
-    long long cap = (long long)((kStaticBytes - off - (size_t)arrays * 256) / ((size_t)arrays * 4));
+    const int rs = rec_stride(p.maxarity);
+    const int words = rs + 4;  // record, nfs, ring, fq0, fq1 (the frontier buffers double as stacks)
+    if (off + (size_t)5 * 256 >= kStaticBytes) return 0;
+    long long cap = (long long)((kStaticBytes - off - (size_t)5 * 256) / ((size_t)words * 4));
     cap = cap / 64 * 64;
     auto take = [&](size_t n) { unsigned char *at = base + off; off = up(off + n); return (int32_t *)at; };
     const size_t s = (size_t)cap * 4;
-    d->hs = take(s);
-    d->args = take(s * ma);
-    d->rc = take(s);
+    d->rec = take(s * rs);
+    d->rs = rs;
     d->nfs = take(s);
-    d->par = take(s);
-    d->pend = take(s);
     d->ring = take(s);
     d->fq[0] = take(s);
     d->fq[1] = take(s);
@@ -85,27 +82,23 @@ __global__ void k_static_upload(DevPool P, const int32_t *term, long long len, i
     Ctl *c = P.ctl;
     const int32_t *ar = P.tab + P.tab[4];  // arity in the low byte of each word
     const int32_t nsym = P.tab[1];
-    P.hs[0] = 0;
+    for (int w = 0; w < P.rs; w++) P.rec[w] = 0;
     P.nfs[0] = 0;
-    P.rc[0] = 0;
-    P.par[0] = 0;
-    P.pend[0] = 0;
     long long sp = 0;
     for (long long q = 0; q < len; q++) {
         const int32_t s = term[q];
         if (s <= 0 || s >= nsym || (q > 0 && sp == 0)) { c->status = TRS_ERR_BAD_TERM; return; }
         const int32_t node = (int32_t)(q + 1);
-        P.hs[node] = s;
-        P.rc[node] = 1;
+        for (int w = 0; w < P.rs; w++) node_at(P, node)[w] = 0;
+        hs_at(P, node) = s;
+        rc_at(P, node) = 1;
         P.nfs[node] = -1;
-        P.pend[node] = 0;
-        P.par[node] = 0;
         if (sp > 0) {
             int32_t parent = stk_node[sp - 1];
             int32_t j = stk_next[sp - 1]++;
-            P.args[(long long)j * P.cap + parent] = node;
-            P.par[node] = parent;
-            if (stk_next[sp - 1] == (ar[P.hs[parent]] & 0xff)) sp--;
+            arg_at(P, j, parent) = node;
+            par_at(P, node) = parent;
+            if (stk_next[sp - 1] == (ar[hs_at(P, parent)] & 0xff)) sp--;
         }
         if ((ar[s] & 0xff) > 0) { stk_node[sp] = node; stk_next[sp] = 0; sp++; }
     }
@@ -128,12 +121,12 @@ __global__ void k_static_download(DevPool P, int32_t *out, long long out_cap, lo
     stk[sp++] = 1;
     while (sp > 0) {
         const int32_t x = stk[--sp];
-        const int32_t s = P.hs[x];
+        const int32_t s = hs_at(P, x);
         if (n >= out_cap) { c->status = TRS_ERR_BUFFER_SMALL; *out_len = -1; return; }
         out[n++] = s;
         for (int a = (ar[s] & 0xff) - 1; a >= 0; a--) {
             if (sp >= P.cap) { c->status = TRS_ERR_BUFFER_SMALL; *out_len = -1; return; }
-            stk[sp++] = P.args[(long long)a * P.cap + x];
+            stk[sp++] = arg_at(P, a, x);
         }
     }
     *out_len = n;

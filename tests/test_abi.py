@@ -90,6 +90,11 @@ def test_pool_bytes_scale(trs):
     assert trs.lib.trs_pool_bytes(p._h, 1 << 20, ctypes.byref(b1)) == 0
     assert trs.lib.trs_pool_bytes(p._h, 1 << 21, ctypes.byref(b2)) == 0
     per_slot = (b2.value - b1.value) / (1 << 20)
-    # head + 2 argument arrays + count + stamp + parent + pending + ring + 2 frontier + trace
-    assert 40 <= per_slot <= 48
+    # 32-byte node record (head, 2 arguments, parent, count, pending, padding)
+    # + stamp + ring + 2 frontier buffers + trace
+    assert per_slot == 52
+    p5 = trs.trs_compile(ti.MSORT)   # arity 5: a 64-byte record
+    assert trs.lib.trs_pool_bytes(p5._h, 1 << 20, ctypes.byref(b1)) == 0
+    assert trs.lib.trs_pool_bytes(p5._h, 1 << 21, ctypes.byref(b2)) == 0
+    assert (b2.value - b1.value) / (1 << 20) == 84
     assert trs.lib.trs_pool_bytes(p._h, 1, ctypes.byref(b1)) == trs.CODE["TRS_ERR_ARG"]
