@@ -268,8 +268,11 @@ def run_ours(args, rank, ws, local):
         out = pool.term_download(r)
         t1 = time.perf_counter()
         e2e_times.append(t1 - t0)
-        h2d = len(term) * 4 * (4 + prog.maxarity) + 8
-        d2h = st["high_water"] * 4 * (1 + prog.maxarity) + 8
+        # node records (rs words) and stamps of the term, the new high-water
+        # mark; the root's stamp and count, then every record below the mark
+        rs = 8 if prog.maxarity + 4 <= 8 else 16
+        h2d = len(term) * 4 * (rs + 1) + 8
+        d2h = 8 + st["high_water"] * 4 * rs
         assert len(out) == 17712
     e2e = rewrites * ws / reduce_max(statistics.mean(e2e_times))
 

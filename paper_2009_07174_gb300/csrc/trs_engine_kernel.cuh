@@ -10,6 +10,7 @@ namespace trs {
 
 struct Flags {
     bool done, gc, confirm, stop, refresh;
+    bool stall;  // learned mode: the sweep changed nothing
 };
 
 
@@ -91,7 +92,7 @@ __device__ __forceinline__ unsigned long long read_u64_block(const unsigned long
 // nothing).  A pure function of (S, V): every block computes the same result.
 __device__ Flags end_sweep(State &S, const AccVals &V, const LaunchOpts &o, long long cap)
 {
-    Flags F{false, false, false, false, false};
+    Flags F{false, false, false, false, false, false};
     // the sweep's allocation positions: the first `avail` were ring entries,
     // the rest fresh slots above the mark; unused ones came back behind fe
     const long long avail = S.fe - S.fb;
@@ -115,6 +116,7 @@ __device__ Flags end_sweep(State &S, const AccVals &V, const LaunchOpts &o, long
         // changed nothing, or every `refresh` sweeps
         S.since += 1;
         F.refresh = S.fsz == 0 || !action || S.since >= o.refresh;
+        F.stall = !action;
     }
     // collection trigger: the plain sweep scans every slot below the high-water
     // mark, so it collects early (dead >= n / 8 by default) to keep the mark
@@ -217,7 +219,7 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
     }
 
     for (long long ran = 0; ran < budget;) {
-        Flags F{false, false, false, false, false};
+        Flags F{false, false, false, false, false, false};
         const bool solo = o.mode != M_PLAIN && o.solo_max > 0 && S.fsz > 0 && S.fsz <= o.solo_max;
         if (start_refresh) {
             start_refresh = false;
@@ -251,7 +253,7 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
                     memset(&ctl->acc[(S.k + 1) % 3], 0, sizeof(Acc));
                     store_state(ctl, S);
                     ctl->solo_flags = (int)F.done | ((int)F.gc << 1) | ((int)F.confirm << 2) |
-                                      ((int)F.stop << 3) | ((int)F.refresh << 4);
+                                      ((int)F.stop << 3) | ((int)F.refresh << 4) | ((int)F.stall << 5);
                     ctl->solo_ran = mine;
                     __threadfence();
                     red_release_add_u32(&ctl->solo_gen, 1u);
@@ -280,6 +282,7 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
             F.confirm = (fl >> 2) & 1;
             F.stop = (fl >> 3) & 1;
             F.refresh = (fl >> 4) & 1;
+            F.stall = (fl >> 5) & 1;
             ran += ldcg_s64(&ctl->solo_ran);
             if (F.done) { finished = true; goto out; }
             if (F.stop || __ldcg(&ctl->status) != 0) goto out;
@@ -366,8 +369,10 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
             S.since = 0;
             if (pend == 0) { finished = true; goto out; }  // a full scan found no work
             S.fsz = sel;
-            if (sel == 0) {
-                // the predictor selected nothing: fall back to the ready nodes
+            if (sel == 0 || F.stall) {
+                // the predictor selected nothing, or its last frontier made no
+                // progress (it may hold only nodes that wait for others, and
+                // would be selected again): take the ready nodes instead
                 phase_seed(P, T, S, A, blockIdx.x, gridDim.x);
                 if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
                 S.fsz = (long long)read_u64_block(&A->conf_found);

@@ -231,3 +231,74 @@ def test_trained_predictor_visits_fewer_nodes_than_plain(env):
     assert np.array_equal(res["plain"][1], res["learned"][1])
     assert res["learned"][0]["rewrites"] == res["plain"][0]["rewrites"]
     assert res["learned"][0]["visits"] < 0.5 * res["plain"][0]["visits"]
+
+
+@pytest.mark.parametrize("t", [ti.FIB, ti.MSORT])
+def test_learned_mode_on_specialised_engine(env, t):
+    """The learned frontier on the engine specialised to the rules: the same
+    normal forms and counts as the oracle, and the stats say which engine
+    ran."""
+    torch, trs = env
+    if t is ti.FIB:
+        terms = [ti.fib_term(n) for n in (0, 3, 11, 17)]
+        train = [ti.fib_term(n) for n in range(8, 17)]
+    else:
+        terms = [ti.msort_batch(seed=3, nlists=4, lmin=2, lmax=30, vmax=9)[0]]
+        train = terms
+    prog = trs.trs_compile(t).specialise()
+    pred = trained_predictor(torch, trs, prog, t, train, period=8)
+    o = Oracle(t)
+    want = [o.normalize(x) for x in terms]
+    for thr in (0.0, 0.5, 1.01):
+        pool = trs.Pool(prog, 1 << 22)
+        pool.trs_pool_attach_predictor(pred)
+        flat, offs = ti.concat_terms(terms)
+        roots = pool.term_upload_batch(flat, offs)
+        st = pool.trs_normalize(mode="learned", threshold=thr, refresh=16)
+        assert st["specialised"] == 1
+        for g, w in zip(pool.term_download_batch(roots), want):
+            assert np.array_equal(g, w.term), thr
+        assert st["rewrites"] == sum(w.rewrites for w in want)
+        assert st["nf_marks"] == sum(w.nf_marks for w in want)
+
+
+@pytest.mark.parametrize("spec", [False, True])
+def test_learned_mode_progress_with_waiting_only_predictor(env, spec):
+    """A predictor that selects exactly the nodes still waiting for their
+    first argument (plus or fib over an argument not in normal form) gives
+    frontiers on which no sweep can act; the engine must still reach the
+    normal form (a sweep that changes nothing re-seeds from the ready
+    nodes), well inside the call's time limit."""
+    torch, trs = env
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    if spec:
+        prog.specialise()
+    pred = trs.Predictor(prog, seed=1)
+    nsym, ma, H = t.nsym, int(max(t.arity)), 32
+    d, sizes = mlp.dims(nsym, ma, H)
+    theta = np.zeros(pred.nparams, dtype=np.float32)
+    W1 = np.zeros((H, d), dtype=np.float32)
+    W1[0, t.id["plus"]] = 1.0
+    W1[0, t.id["fib"]] = 1.0
+    W1[0, nsym * (1 + ma) + 0] = -1.0      # argument 0 in normal form
+    W2 = np.zeros((H, H), dtype=np.float32)
+    W2[0, 0] = 1.0
+    w3 = np.zeros(H, dtype=np.float32)
+    w3[0] = 20.0
+    theta[:] = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), w3, [-10.0]])
+    pred.set_params(theta)
+    feat = np.array([[t.id["plus"], t.id["S"], t.id["0"], 0b10], [t.id["plus"], t.id["S"], t.id["0"], 0b11],
+                     [t.id["S"], t.id["0"], 0, 0b0]], dtype=np.int32)
+    p = mlp.prob(theta.astype(np.float64), feat, nsym, ma, H)
+    assert p[0] > 0.99 and p[1] < 0.01 and p[2] < 0.01
+    terms = [ti.fib_term(n) for n in (4, 10, 13)]
+    want = [Oracle(t).normalize(x) for x in terms]
+    pool = trs.Pool(prog, 1 << 20)
+    pool.trs_pool_attach_predictor(pred)
+    flat, offs = ti.concat_terms(terms)
+    roots = pool.term_upload_batch(flat, offs)
+    st = pool.trs_normalize(mode="learned", threshold=0.5, refresh=4, time_limit_ns=20_000_000_000)
+    for g, w in zip(pool.term_download_batch(roots), want):
+        assert np.array_equal(g, w.term)
+    assert st["rewrites"] == sum(w.rewrites for w in want)
