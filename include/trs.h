@@ -105,11 +105,10 @@ int32_t trs_program_maxarity(const trs_program *prog);
 /* Specialised engine (the paper's generated rewrite code, Sec. 3).  Writes the
  * matcher and rewriter of every rule of `prog` as straight-line CUDA C++,
  * compiles it with the engine's sweep loop by NVRTC for the current device
- * (sm_XYa) and loads it; later trs_normalize calls on pools of `prog` in
- * modes plain, frontier and learned with the persistent or host driver run it
- * (results and counts are those of the table-driven engine; the graph driver
- * and trs_collect_samples keep the table-driven kernel; trs_opts.generic = 1
- * selects it explicitly).  `cache_dir` (may be NULL) keeps compiled images by
+ * (sm_XYa) and loads it; later trs_normalize calls on pools of `prog`, in
+ * every mode and with every driver, and trs_collect_samples, run it (normal
+ * forms and counts are those of the table-driven engine; trs_opts.generic = 1
+ * selects the table-driven one).  `cache_dir` (may be NULL) keeps compiled images by
  * content hash.  Needs libnvrtc at run time and the CUDA include directory
  * ($TRS_CUDA_INCLUDE, $CUDA_HOME/include or /usr/local/cuda/include).  Takes
  * seconds on a cache miss.  Not thread-safe for one program.  Returns TRS_OK,

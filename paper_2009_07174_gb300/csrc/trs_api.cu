@@ -21,6 +21,7 @@ cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream);
 cudaError_t reset_launch(const DevPool &P, cudaStream_t stream);
 cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t stream);
 void *engine_kernel_ptr(int mode);
+void *graph_cond_ptr();
 const unsigned char *predictor_block(const trs_predictor *p);
 size_t predictor_block_bytes(const trs_predictor *p);
 const trs_program *predictor_program(const trs_predictor *p);
@@ -33,6 +34,7 @@ struct GraphCache {
     LaunchOpts key{};
     long long budget = 0;
     const unsigned char *mlp = nullptr;
+    const void *fn = nullptr;  // engine kernel of the graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -308,10 +310,10 @@ static bool same_key(const LaunchOpts &a, const LaunchOpts &b)
 // Build (once per launch configuration) a graph whose only node is a while
 // loop around the engine kernel; the kernel clears the loop condition when the
 // normalisation ends or fails.
-static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, long long budget)
+static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, long long budget, const void *fn)
 {
     GraphCache &G = pool->graph;
-    if (G.valid && same_key(G.key, o) && G.budget == budget && G.mlp == dp.mlp) return TRS_OK;
+    if (G.valid && same_key(G.key, o) && G.budget == budget && G.mlp == dp.mlp && G.fn == fn) return TRS_OK;
     if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
     if (G.graph) { cudaGraphDestroy(G.graph); G.graph = nullptr; }
     G.valid = false;
@@ -332,7 +334,7 @@ static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, l
     unsigned long long cond = (unsigned long long)handle;
     void *kargs[4] = {&P, &lo, &bud, &cond};
     cudaKernelNodeParams kp = {};
-    kp.func = engine_kernel_ptr(o.mode);
+    kp.func = fn ? (void *)fn : engine_kernel_ptr(o.mode);
     kp.gridDim = dim3((unsigned)o.grid);
     kp.blockDim = dim3((unsigned)o.block);
     kp.sharedMemBytes = (unsigned)engine_smem_bytes(dp, o.mode, o.block);
@@ -342,10 +344,21 @@ static int build_graph(trs_pool *pool, const DevPool &dp, const LaunchOpts &o, l
     cudaLaunchAttributeValue v = {};
     v.cooperative = 1;
     CK(cudaGraphKernelNodeSetAttribute(kn, cudaLaunchAttributeCooperative, &v), "cooperative attribute");
+    // the loop condition is cleared by a one-thread kernel after the engine
+    // (engines compiled at run time cannot call the device runtime)
+    void *cargs[2] = {&P, &cond};
+    cudaKernelNodeParams cq = {};
+    cq.func = graph_cond_ptr();
+    cq.gridDim = dim3(1);
+    cq.blockDim = dim3(1);
+    cq.kernelParams = cargs;
+    cudaGraphNode_t cn;
+    CK(cudaGraphAddKernelNode(&cn, body, &kn, 1, &cq), "condition node");
     CK(cudaGraphInstantiate(&G.exec, G.graph, 0), "graph instantiate");
     G.key = o;
     G.budget = budget;
     G.mlp = dp.mlp;
+    G.fn = fn;
     G.valid = true;
     return TRS_OK;
 }
@@ -366,10 +379,9 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
         d.mlp = predictor_block(pool->pred);
         d.mlp_bytes = (int32_t)predictor_block_bytes(pool->pred);
     }
-    // the engine specialised to this program's rules, when there is one (the
-    // graph driver's loop condition is cleared by the table-driven kernel)
+    // the engine specialised to this program's rules, when there is one
     const void *fn = nullptr;
-    if (!o.generic && pool->prog->spec && o.driver != TRS_DRIVER_GRAPH) fn = spec_kernel(pool->prog->spec, o.mode);
+    if (!o.generic && pool->prog->spec) fn = spec_kernel(pool->prog->spec, o.mode);
     const size_t smem = engine_smem_bytes(d, o.mode, o.block_size);
     int bps = 0;
     CK(engine_configure(o.mode, o.block_size, smem, &bps, fn), "occupancy");
@@ -396,7 +408,7 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
     if (o.driver == TRS_DRIVER_PERSISTENT) {
         CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream, fn), "engine launch");
     } else if (o.driver == TRS_DRIVER_GRAPH) {
-        int st = build_graph(pool, d, lo, o.graph_unroll);
+        int st = build_graph(pool, d, lo, o.graph_unroll, fn);
         if (st != TRS_OK) return st;
         CK(cudaGraphLaunch(pool->graph.exec, stream), "graph launch");
     } else {
@@ -452,7 +464,9 @@ int trs_collect_samples(trs_pool *pool, const trs_opts *opts, int32_t period, fl
     d.samp_label = (float *)((char *)dev_samples + feat_b + ((size_t)cap * 4 + 255) / 256 * 256);
     d.samp_cap = cap;
     int bps = 0;
-    CK(engine_configure(o.mode, o.block_size, engine_smem_bytes(d, o.mode, o.block_size), &bps), "occupancy");
+    const void *fn = nullptr;
+    if (!o.generic && pool->prog->spec) fn = spec_kernel(pool->prog->spec, o.mode);
+    CK(engine_configure(o.mode, o.block_size, engine_smem_bytes(d, o.mode, o.block_size), &bps, fn), "occupancy");
     if (bps <= 0) { set_error("trs_collect_samples: kernel does not fit on an SM"); return TRS_ERR_CUDA; }
     LaunchOpts lo{};
     lo.mode = o.mode;
@@ -470,7 +484,7 @@ int trs_collect_samples(trs_pool *pool, const trs_opts *opts, int32_t period, fl
     lo.sample_thresh = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
     lo.sample_seed = (uint32_t)(seed ^ (seed >> 32));
     CK(prep_launch(pool->d.ctl, o.max_sweeps, o.mode != TRS_MODE_PLAIN ? 1 : 0, stream), "prepare");
-    CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream), "engine launch");
+    CK(engine_launch(d, lo, LLONG_MAX, 0ull, stream, fn), "engine launch");
     Ctl h;
     int st = read_ctl(pool, &h, stream);
     if (st != TRS_OK) return st;

@@ -126,4 +126,17 @@ cudaError_t prep_launch(Ctl *ctl, long long max_sweeps, int seed, cudaStream_t s
 
 void *engine_kernel_ptr(int mode) { return engine_fn(mode); }
 
+// Graph driver: clear the while-loop condition once the normalisation has
+// ended or failed.  A node of its own after the engine kernel, so that the
+// engines compiled at run time (which cannot call the device runtime) share
+// the graph driver.
+__global__ void k_graph_cond(DevPool P, unsigned long long cond)
+{
+    const Ctl *ctl = P.ctl;
+    if (__ldcg(&ctl->done) || __ldcg(&ctl->status) != 0)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 0);
+}
+
+void *graph_cond_ptr() { return (void *)k_graph_cond; }
+
 }  // namespace trs

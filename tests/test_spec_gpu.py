@@ -98,10 +98,11 @@ def test_eager_and_solo(trs, eager, solo):
           solo_max=solo)
 
 
-def test_host_driver_and_generic_switch(trs):
+def test_drivers_and_generic_switch(trs):
     prog = program(trs, ti.FIB)
     want = Oracle(ti.FIB).normalize(ti.fib_term(12))
-    for kw, spec in ((dict(driver="host"), 1), (dict(generic=1), 0), (dict(driver="graph"), 0)):
+    for kw, spec in ((dict(driver="host"), 1), (dict(generic=1), 0), (dict(driver="graph"), 1),
+                     (dict(driver="graph", graph_unroll=3, eager=16), 1), (dict(driver="graph", generic=1), 0)):
         pool = trs.Pool(prog, 1 << 16)
         r = pool.term_upload(ti.fib_term(12))
         st = pool.trs_normalize(mode="frontier", **kw)
