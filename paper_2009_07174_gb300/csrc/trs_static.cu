@@ -185,8 +185,11 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
         return fail("trs_normalize_static: term of " + std::to_string(len) + " symbols exceeds the " +
                     std::to_string(cap - 1) + "-slot static node store", TRS_ERR_TOO_BIG);
     int sms = 0, bps = 0;
+    // the engine specialised to the program's rules, when there is one
+    const void *fn = (!o.generic && prog->spec) ? spec_kernel(prog->spec, o.mode) : nullptr;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = engine_configure(o.mode, o.block_size, engine_smem_bytes(d, o.mode, o.block_size), &bps);
+    if (e == cudaSuccess)
+        e = engine_configure(o.mode, o.block_size, engine_smem_bytes(d, o.mode, o.block_size), &bps, fn);
     if (e != cudaSuccess || bps <= 0) return fail("trs_normalize_static: occupancy query failed", TRS_ERR_CUDA);
     LaunchOpts lo{};
     lo.mode = o.mode;
@@ -212,7 +215,7 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
     // do nothing
     k_static_upload<<<1, 1, 0, stream>>>(d, d_term, len, d.fq[0], d.fq[1]);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = engine_launch(d, lo, LLONG_MAX, 0ull, stream);
+    if (e == cudaSuccess) e = engine_launch(d, lo, LLONG_MAX, 0ull, stream, fn);
     if (e != cudaSuccess) return fail(std::string("trs_normalize_static: ") + cudaGetErrorString(e), TRS_ERR_CUDA);
     k_static_download<<<1, 1, 0, stream>>>(d, d_out, out_cap, (long long *)d_out_len, d.fq[0]);
     e = cudaGetLastError();
@@ -236,6 +239,7 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
         stats->frontier_peak = h.st_frontier_peak;
         stats->high_water = h.n_top;
         stats->solo_sweeps = h.st_solo_sweeps;
+        stats->specialised = fn != nullptr;
     }
     if (h.status != 0) return fail("trs_normalize_static: device status " + std::to_string(h.status), h.status);
     set_error("");

@@ -43,18 +43,25 @@ def via_static(torch, trs, prog, term, mode):
     return d_out[:n].cpu().numpy(), st
 
 
+@pytest.mark.parametrize("spec", [False, True])
 @pytest.mark.parametrize("mode", ["plain", "frontier"])
-def test_static_matches_pool_two_calls(env, mode):
+def test_static_matches_pool_two_calls(env, mode, spec):
+    """Both engines: the table-driven one, and the one specialised to the
+    rules (compiled before the calls; the calls themselves allocate
+    nothing)."""
     torch, trs = env
     cases = [(ti.FIB, ti.fib_term(15)), (ti.FIB, ti.fib_term(11))]
     term, _ = ti.msort_batch(seed=4, nlists=4, lmin=3, lmax=20, vmax=9)
     cases.append((ti.MSORT, term))
     for t, term in cases:
         prog = trs.trs_compile(t)
+        if spec:
+            prog.specialise()
         want, st_want = via_pool(trs, prog, term, mode)
         for _ in range(2):       # two calls in a row share the array
             got, st = via_static(torch, trs, prog, term, mode)
             assert np.array_equal(got, want)
+            assert st["specialised"] == int(spec) == st_want["specialised"]
             for k in ("rewrites", "nf_marks", "sweeps", "allocs"):
                 assert st[k] == st_want[k], (k, st, st_want)
 
