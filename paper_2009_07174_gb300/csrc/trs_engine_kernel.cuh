@@ -192,7 +192,16 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
     }
     State S = load_state(ctl);
     const long long k_first = S.k;
-    long long s_lo = 0, s_hi = 0, s_k = -1;  // predictor traces: current batch of rows
+    // predictor traces: the current batch of rows [s_lo, s_hi) and the sweep
+    // it was sampled in; block-uniform, kept in shared memory (written by
+    // thread 0 between barriers) so that it takes no registers
+    __shared__ long long s_trace_rows[3];
+    long long &s_lo = s_trace_rows[0], &s_hi = s_trace_rows[1], &s_k = s_trace_rows[2];
+    if (threadIdx.x == 0) {
+        s_lo = 0;
+        s_hi = 0;
+        s_k = -1;
+    }
     const bool b0 = blockIdx.x == 0, t0 = b0 && threadIdx.x == 0;
     const unsigned nblocks = gridDim.x;
     const long long wpb = blockDim.x >> 5;
@@ -200,7 +209,11 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
     const long long gnw = (long long)gridDim.x * wpb;
     unsigned solo_gen = __ldcg(&ctl->solo_gen);
     bool finished = false;
-    LocalStats L{};
+    // statistics of this launch: kept by thread 0 of block 0 only, in shared
+    // memory so that they occupy no registers in the sweep loop
+    __shared__ LocalStats s_stats;
+    LocalStats &L = s_stats;
+    if (threadIdx.x == 0) L = LocalStats{};
     // seed requests are read by every block before anyone clears them
     const int phase0 = __ldcg(&ctl->mode_phase);
     // initial frontier, learned mode: a refresh scores the whole store
@@ -292,10 +305,14 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
                 if (s_k >= 0) phase_label(P, s_lo, s_hi, S.k);
                 phase_sample(P, T, S, o);
                 if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
-                s_lo = s_hi;
-                s_hi = (long long)read_u64_block((const unsigned long long *)&ctl->samp_n);
-                if (s_hi > P.samp_cap) s_hi = P.samp_cap;
-                s_k = S.k;
+                long long hi = (long long)read_u64_block((const unsigned long long *)&ctl->samp_n);
+                if (hi > P.samp_cap) hi = P.samp_cap;
+                if (threadIdx.x == 0) {
+                    s_lo = s_hi;
+                    s_hi = hi;
+                    s_k = S.k;
+                }
+                __syncthreads();
             }
             // ---- one grid-wide sweep
             if (t0) memset(&ctl->acc[(S.k + 1) % 3], 0, sizeof(Acc));
