@@ -666,12 +666,14 @@ __device__ __forceinline__ void spec_apply(const DevPool &P, const Tab &T, int m
 __device__ __forceinline__ int spec_new_count(int d);
 #endif
 
+constexpr int kClimb = 64;  // levels of one constructor climb
+
 // One decision + allocation + application + push for every lane of a warp
 // (lane-uniform control flow; `cand` marks lanes with a node to consider).
 __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, const State &S,
                                                 Acc *A, WarpAlloc &W, int mode, bool cand, bool keep,
                                                 int32_t i, bool check_ready, int32_t *next_buf,
-                                                Counters &C, bool eager, Carry &carry)
+                                                Counters &C, bool eager, Carry &carry, bool climb = false)
 {
     int32_t reg[TRS_MAX_PATTERN];
     int32_t nw[TRS_MAX_RHS];
@@ -716,6 +718,45 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     if (eager && npush > 0) {
         cont = push[--npush];
         carry = last;
+    }
+    // Constructor climb (frontier mode, eager, small frontiers): when node i
+    // became a normal form and its unary parent is the continuation, the
+    // parent is ready; if its head has no rules it is a normal form too, and so
+    // on up the chain.
+    // Each level costs one load of the parent's first record words (head,
+    // argument, parent word up to arity 2) instead of a step.  The climb stops
+    // at a head with rules (handed on as the continuation, its one argument
+    // carried), at a binary parent (pending count, as a step would) or after
+    // kClimb levels.  Marks and stamps are those the steps would write.
+    // Only for solo episodes: with a wide frontier a lane that climbs keeps
+    // its warp from taking new entries.
+    if (climb && mode == M_FRONTIER && eager && cont >= 0 && carry.h == 0 && (d == D_MARK || d >= 0) &&
+        pv < 0 && cont == (pv & 0x7fffffff)) {
+        int32_t child = i, p = cont;
+        for (int lvl = 0; lvl < kClimb; lvl++) {
+            const int4 q = rec_head4(P, p);
+            const int32_t ph = q.x;
+            if (T.first(ph) != T.first(ph + 1)) {
+                cont = p;
+                carry.h = ph;
+                carry.c[0] = child;
+                break;
+            }
+            P.nfs[p] = (int32_t)(S.k + 1);
+            C.nf_marks++;
+            const int32_t ppv = rec_ma(P) == 2 ? q.w : par_at(P, p);
+            const int32_t pp = ppv & 0x7fffffff;
+            cont = -1;
+            if (pp == 0) break;
+            if (ppv >= 0) {
+                if (atom_acqrel_add_s32(&pend_at(P, pp), -1) == 1) cont = pp;
+                break;
+            }
+            child = p;
+            p = pp;
+            cont = p;
+            if (lvl + 1 == kClimb) break;
+        }
     }
     if (mode != M_PLAIN && __any_sync(kFull, npush > 0))
         warp_push(next_buf, &A->pushes, P.cap, npush, push, P.ctl);
@@ -803,7 +844,7 @@ __device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, cons
 // steps per sweep.  Results and counts are those of the synchronous sweep;
 // only the number of sweeps changes.
 __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
-                               long long warp0, long long nwarps, int eager = 0)
+                               long long warp0, long long nwarps, int eager = 0, bool climb = false)
 {
     Counters C{0, 0, 0, 0, 0};
     WarpAlloc W = warp_alloc_begin(P, S);
@@ -877,7 +918,7 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                 continue;
             }
             int32_t cont = process_warp(P, T, S, A, W, mode, cand, false, cand ? node : 0, false, next, C,
-                                        true, carry);
+                                        true, carry, climb);
             steps++;
             const bool over = cont >= 0 && (steps >= eager || pressure);
             if (__any_sync(kFull, over)) warp_push(next, &A->pushes, P.cap, over ? 1 : 0, &cont, P.ctl);

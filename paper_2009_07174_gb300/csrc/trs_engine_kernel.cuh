@@ -245,7 +245,7 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
                 for (;;) {
                     if (threadIdx.x == 0) memset(&s_acc, 0, sizeof(Acc));
                     __syncthreads();
-                    phase_frontier(P, T, S, &s_acc, o.mode, threadIdx.x >> 5, wpb, o.eager);
+                    phase_frontier(P, T, S, &s_acc, o.mode, threadIdx.x >> 5, wpb, o.eager, true);
                     __syncthreads();
                     const AccVals V = read_acc(&s_acc, true);
                     F = end_sweep(S, V, o, P.cap);
