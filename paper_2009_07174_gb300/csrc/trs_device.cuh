@@ -115,8 +115,6 @@ struct Tab {
     const int32_t *w;
     int off_ar, off_first, off_rules;
     __device__ __forceinline__ int arity(int s) const { return w[off_ar + s] & 0xff; }
-    // prefetch plan of head s: what its patterns read two levels down
-    __device__ __forceinline__ int plan(int s) const { return w[off_ar + s] >> 8; }
     __device__ __forceinline__ int first(int s) const { return w[off_first + s]; }
     __device__ __forceinline__ const int32_t *rule(int r) const { return w + off_rules + r * kRuleWords; }
 };

@@ -71,7 +71,6 @@ struct Program {
 struct Acc {  // per-sweep accumulators, triple-buffered by sweep number % 3
     unsigned long long rewrites, nf_marks, visits, allocs;
     unsigned long long fl_claims;  // allocation positions claimed in this sweep
-    unsigned long long fresh;      // (unused)
     unsigned long long deaths;     // reference counts that reached zero
     unsigned long long pushes;     // entries written to the next frontier
     unsigned long long gc_frees, gc_deaths, gc_append;  // garbage collection
@@ -96,7 +95,6 @@ struct Ctl {
     int mode_phase;       // 1 = seed the frontier at the next launch
     int solo_flags;       // outcome of the last solo episode: done | gc << 1 | confirm << 2 | stop << 3
     long long solo_ran;   // sweeps run by the last solo episode
-    long long since_refresh;
     // statistics of the current trs_normalize
     long long st_rewrites, st_nf_marks, st_sweeps, st_visits, st_allocs, st_frees;
     long long st_gc_runs, st_confirm, st_confirm_found, st_refreshes, st_frontier_peak;
