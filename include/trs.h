@@ -3,8 +3,9 @@
  *
  * The engine normalises ground terms under a term rewrite system (TRS) with the
  * parallel innermost method of "Term Rewriting on GPUs" (arxiv 2009.07174):
- * terms live in a structure-of-arrays node store (head symbol, one index array
- * per argument position, normal-form stamp, reference count), and repeated
+ * terms live in a node store (a record per node with its head symbol, argument
+ * indices and reference count, beside an array of normal-form stamps; the
+ * paper keeps one array per field, Sec. 3), and repeated
  * sweeps rewrite, in place, every node that is not in normal form and whose
  * arguments all are (Sec. 3, the derive kernel), taking new nodes from a free
  * list or above the high-water mark (Sec. 3, get_new_index) and reclaiming
