@@ -664,7 +664,8 @@ __device__ __forceinline__ void spec_apply(const DevPool &P, const Tab &T, int m
 __device__ __forceinline__ int spec_new_count(int d);
 #endif
 
-constexpr int kClimb = 64;  // levels of one constructor climb
+constexpr int kClimb = 64;    // levels of one constructor climb
+constexpr int kInPlace = 64;  // steps of one constant chain
 
 // One decision + allocation + application + push for every lane of a warp
 // (lane-uniform control flow; `cand` marks lanes with a node to consider).
@@ -716,6 +717,42 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     if (eager && npush > 0) {
         cont = push[--npush];
         carry = last;
+    }
+    // Constant chain (frontier mode, eager): when the continuation is node i
+    // itself, rewritten in place to a constant (a renaming such as A -> B),
+    // the constant's own rule is applied here as long as it needs no new slot.
+    // Only constants: chains of rules with arguments (a comparison walking
+    // down two numerals) differ in length from lane to lane and would hold a
+    // warp's other lanes back.
+    if (eager && mode == M_FRONTIER && cont == i && carry.h != 0 && npush == 0 && T.arity(carry.h) == 0 &&
+        T.first(carry.h) != T.first(carry.h + 1)) {
+        for (int n = 0; n < kInPlace; n++) {
+            int32_t h2 = 0;
+#ifdef TRS_JIT
+            const int d2 = spec_decide(P, T, i, S.k, false, reg, h2, carry);
+            if (d2 < 0 || spec_new_count(d2) > 0) break;
+#else
+            const int d2 = decide(P, T, i, S.k, false, reg, h2, carry);
+            if (d2 < 0 || ((T.rule(d2)[0] >> 8) & 0xff) > 0) break;
+#endif
+            Carry last2;
+            last2.h = 0;
+            C.visits++;
+#ifdef TRS_JIT
+            spec_apply(P, T, mode, i, h2, pv, d2, S.k, reg, nw, C, push, npush, last2);
+#else
+            apply(P, T, mode, i, h2, pv, d2, S.k, reg, nw, C, push, npush, last2);
+#endif
+            cont = -1;
+            carry.h = 0;
+            if (npush > 0) {
+                cont = push[--npush];
+                carry = last2;
+            }
+            if (cont != i || carry.h == 0 || npush != 0 || T.arity(carry.h) != 0 ||
+                T.first(carry.h) == T.first(carry.h + 1))
+                break;
+        }
     }
     // Constructor climb (frontier mode, eager, small frontiers): when node i
     // became a normal form and its unary parent is the continuation, the

@@ -69,6 +69,10 @@ def test_merge_sort(trs):
 
 def test_transformation_tree(trs):
     check(trs, ti.TTREE, [ti.ttree_term(n) for n in range(0, 9)])
+    # eager: the letter renamings run as constant chains within one step
+    for kw in (dict(eager=64), dict(eager=64, solo_max=512), dict(eager=4)):
+        check(trs, ti.TTREE, [ti.ttree_term(n) for n in range(0, 12)], modes=("frontier",),
+              check_sweeps=False, **kw)
 
 
 def test_wide_patterns(trs):
