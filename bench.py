@@ -17,6 +17,7 @@ of the term (a single term does not shard: replicas only).
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -145,7 +146,9 @@ def profiled_traffic(name, units=None):
     for line in open(path):
         if "=" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split("=", 1)
-            vals[k.strip().strip("`")] = v.strip().strip("`")
+            # the value is the first `quoted` token (a remark may follow it)
+            m = re.search(r"`([^`]*)`", v)
+            vals[k.strip().strip("`")] = m.group(1) if m else v.strip()
     if vals.get("source_sha256") != kernel_source_hash():
         return None
     try:

@@ -1,0 +1,86 @@
+"""Host-side pieces of the benchmark (no GPU): the profile records the
+roofline's `traffic` field comes from, the algorithmic byte model, and the
+reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.fixture(scope="module")
+def bench():
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        import bench as b
+    finally:
+        sys.argv = argv
+    return b
+
+
+def test_profiled_traffic_reads_committed_records(bench):
+    """Every committed engine summary names the kernel source it was taken
+    on; where that is the current source, its traffic is read back, and a
+    smaller case is scaled by the units it processed."""
+    d = os.path.join(ROOT, "profiles")
+    current = bench.kernel_source_hash()
+    for name in ("k_engine_fib22_frontier", "k_engine_plain_scan"):
+        text = open(os.path.join(d, name + ".md")).read()
+        assert "source_sha256" in text and "traffic_bytes_per_launch" in text
+        if current in text:
+            t = bench.profiled_traffic(name)
+            assert t is not None and t > 0
+    if current in open(os.path.join(d, "k_engine_plain_scan.md")).read():
+        one = bench.profiled_traffic("k_engine_plain_scan")
+        two = bench.profiled_traffic("k_engine_plain_scan", units=2 * 54159727)
+        assert abs(two - 2 * one) <= 2
+
+
+def test_profiled_traffic_is_none_for_other_sources(bench, tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abcd")
+    (prof / "k.md").write_text("- source_sha256 = `0000`\n- traffic_bytes_per_launch = `123`\n")
+    assert bench.profiled_traffic("k") is None
+    (prof / "k.md").write_text("- source_sha256 = `abcd`\n- traffic_bytes_per_launch = `120`\n"
+                               "- units_per_launch = `10` (slots below the mark)\n")
+    assert bench.profiled_traffic("k") == 120
+    assert bench.profiled_traffic("k", units=25) == 300
+    assert bench.profiled_traffic("missing") is None
+
+
+def test_alg_bytes_counts_every_term(bench):
+    st = {"mode": "frontier", "visits": 10, "rewrites": 4, "allocs": 3, "nf_marks": 5, "frees": 2,
+          "gc_runs": 1, "high_water": 100, "confirm_sweeps": 1}
+    b0 = bench.alg_bytes(st, None, 2)
+    # maxarity 2: a node is 12 bytes (head and two arguments)
+    want = 10 * (12 + 8 + 4) + 4 * (12 + 16 + 12) + 3 * (12 + 16) + 5 * 8 + (100 * 8 + 2 * 16) \
+        + 2 * 100 * 4 + 10 * 8
+    assert b0 == want
+    for k in ("visits", "rewrites", "allocs", "nf_marks", "frees"):
+        assert bench.alg_bytes(dict(st, **{k: st[k] + 1}), None, 2) > b0
+    # the plain sweep adds 4 bytes per slot of every sweep's scan (trace column 5)
+    plain = dict(st, mode="plain")
+    assert bench.alg_bytes(plain, [(0, 0, 0, 0, 0, 50), (1, 0, 0, 0, 0, 70)], 2) == \
+        bench.alg_bytes(plain, None, 2) + 120 * 4
+
+
+def test_reference_arm_line(tmp_path):
+    """bench.py --impl reference times the CPU oracle and prints one JSON line
+    with the contract's keys."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--cpu-seconds", "0.5"], capture_output=True, text=True, timeout=300,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "cpu_baseline", "e2e", "impl", "config"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
