@@ -115,6 +115,21 @@ def test_wide_patterns(trs):
     check(trs, ti.WIDE, ti.wide_terms(6, 200, 6), modes=["frontier"], check_sweeps=False, eager=16)
 
 
+def test_arity8_records(trs):
+    """A symbol of the largest arity (64-byte node records), patterns on the
+    last argument, a rule that drops six arguments; nested terms."""
+    check(trs, ti.OCT, ti.oct_terms(3, 200))
+    check(trs, ti.OCT, ti.oct_terms(4, 200), modes=["frontier"], check_sweeps=False, eager=16, solo_max=512)
+
+
+def test_constants_only(trs):
+    """Maximum arity 0: records with no argument words."""
+    c = ti.CONSTS
+    check(trs, c, [c.encode(x) for x in ("a", "b", "c", "d")])
+    check(trs, c, [c.encode(x) for x in ("a", "b", "c", "d")], modes=["frontier"], check_sweeps=False,
+          eager=8, solo_max=512)
+
+
 def test_fib22_plain_and_frontier(trs):
     """fib(22) -> S^17711(0), 186,579 rewrites, node pool of 2^24 slots."""
     want = Oracle(ti.FIB).normalize(ti.fib_term(22))

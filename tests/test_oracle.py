@@ -261,3 +261,20 @@ def test_planted_mistakes_are_caught():
                   (("fib", ("S", ("S", ti.X))), ("plus", ("fib", ti.X), ("fib", ti.X)))])
     r = Oracle(bad).normalize(ti.fib_term(10))
     assert value(ti.FIB, r.term) != fib_numbers(10)[10]
+
+
+@pytest.mark.parametrize("mode", ["innermost", "outermost", "parallel"])
+def test_arity8_closed_form(mode):
+    """k(a, b, c, d, e, f, g, h) over numerals: the first rule moves a into b,
+    the second h into g, the third keeps S(b).  Normal form S^(a+b+1)(0); the
+    innermost count is a + h + 1 (every k redex has numeral arguments)."""
+    t = ti.OCT
+    o = Oracle(t)
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        v = [int(x) for x in rng.integers(0, 8, size=8)]
+        term = t.encode(("k", *(ti.peano_tuple(x) for x in v)))
+        r = o.normalize(term, mode)
+        assert np.array_equal(r.term, ti.peano(t, v[0] + v[1] + 1))
+        if mode == "innermost":
+            assert r.rewrites == v[0] + v[7] + 1

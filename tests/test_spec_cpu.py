@@ -5,7 +5,7 @@ compiles them with the sweep loop by NVRTC.  Here: the generated source names
 every rule of every head in textual order, and the whole engine compiles for
 sm_103a for systems that cover the generator's cases (depth-three patterns,
 patterns on arguments beyond the second, variable right-hand-side roots,
-arity five)."""
+arities zero, five and eight)."""
 import re
 
 import pytest
@@ -21,7 +21,7 @@ def trs():
     return m
 
 
-@pytest.mark.parametrize("t", [ti.FIB, ti.ARITH, ti.MSORT, ti.TTREE, ti.WIDE, ti.PAPER_FFA])
+@pytest.mark.parametrize("t", [ti.FIB, ti.ARITH, ti.MSORT, ti.TTREE, ti.WIDE, ti.OCT, ti.CONSTS, ti.PAPER_FFA])
 def test_generated_rules_in_textual_order(trs, t):
     src = trs.trs_compile(t).specialised_source()
     # the matcher tests each head's rules in textual order
@@ -37,7 +37,7 @@ def test_generated_rules_in_textual_order(trs, t):
     assert sorted(int(x) for x in re.findall(r"case \d+: \{  // rule (\d+)", src)) == list(range(len(t.rules)))
 
 
-@pytest.mark.parametrize("t", [ti.FIB, ti.MSORT, ti.WIDE])
+@pytest.mark.parametrize("t", [ti.FIB, ti.MSORT, ti.WIDE, ti.OCT, ti.CONSTS])
 def test_specialised_engine_compiles(trs, t, tmp_path):
     p = trs.trs_compile(t)
     try:

@@ -79,6 +79,18 @@ def test_wide_patterns(trs):
     check(trs, ti.WIDE, ti.wide_terms(5, 300, 5))
 
 
+def test_arity8_records(trs):
+    check(trs, ti.OCT, ti.oct_terms(3, 200))
+    check(trs, ti.OCT, ti.oct_terms(4, 200), modes=("frontier",), check_sweeps=False, eager=16, solo_max=512)
+
+
+def test_constants_only(trs):
+    c = ti.CONSTS
+    check(trs, c, [c.encode(x) for x in ("a", "b", "c", "d")])
+    check(trs, c, [c.encode(x) for x in ("a", "b", "c", "d")], modes=("frontier",), check_sweeps=False,
+          eager=8, solo_max=512)
+
+
 def test_paper_examples(trs):
     ffa = ti.PAPER_FFA
     check(trs, ffa, [np.array([ffa.id["f"]] * 3 + [ffa.id["a"]], dtype=np.int32)])

@@ -203,6 +203,14 @@ def peano(trs: TRS, n: int) -> np.ndarray:
     return out
 
 
+def peano_tuple(n: int):
+    """The numeral S^n(0) as a nested tuple (for TRS.encode)."""
+    t = "0"
+    for _ in range(n):
+        t = ("S", t)
+    return t
+
+
 def fib_term(n: int) -> np.ndarray:
     return np.concatenate([[FIB.id["fib"]], peano(FIB, n)]).astype(np.int32)
 
@@ -399,3 +407,32 @@ def wide_terms(seed, count, depth):
             return f
         return (f, *(gen(d - 1) for _ in range(ar)))
     return [WIDE.encode(gen(depth)) for _ in range(count)]
+
+
+# A system with one symbol of the largest arity (8): patterns on the first and
+# the last argument, a rule that drops six arguments.  k(a, b, c, d, e, f, g, h)
+# over numerals moves a into b, then h into g, then becomes S(b): its normal
+# form is S^(a+b+1)(0) after a + h + 1 rewrites.
+_V8 = [Var(v) for v in ("a8", "b8", "c8", "d8", "e8", "f8", "g8", "h8")]
+OCT = TRS("oct", [("0", 0), ("S", 1), ("k", 8)], [
+    (("k", ("S", _V8[0]), *_V8[1:]), ("k", _V8[0], ("S", _V8[1]), *_V8[2:])),
+    (("k", "0", *_V8[1:7], ("S", _V8[7])), ("k", "0", *_V8[1:6], ("S", _V8[6]), _V8[7])),
+    (("k", "0", *_V8[1:7], "0"), ("S", _V8[1])),
+])
+
+
+def oct_terms(seed, count, vmax=6, nest=0.2):
+    """Seeded k(...) terms over numerals up to vmax; an argument is itself a
+    k term with probability `nest` (one level)."""
+    rng = np.random.default_rng(seed)
+
+    def arg(depth):
+        if depth == 0 and rng.random() < nest:
+            return ("k", *(arg(1) for _ in range(8)))
+        return peano_tuple(int(rng.integers(0, vmax + 1)))
+    return [OCT.encode(("k", *(arg(0) for _ in range(8)))) for _ in range(count)]
+
+
+# Only constants (maximum arity 0): a -> b -> c, d stays.
+CONSTS = TRS("consts", [("a", 0), ("b", 0), ("c", 0), ("d", 0)],
+             [(("a",), ("b",)), (("b",), ("c",))])
