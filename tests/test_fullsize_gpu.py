@@ -46,29 +46,43 @@ def is_numeral(t, pre, v):
     return len(pre) == v + 1 and pre[-1] == zero and (v == 0 or np.all(pre[:-1] == succ))
 
 
-def test_fib22_all_modes(trs):
-    """Single term fib(22), pool 2^24: plain, exact frontier (synchronous and
-    eager, one block for small frontiers) and learned frontier."""
-    t = ti.FIB
+def program(trs, t, spec):
     prog = trs.trs_compile(t)
+    if spec:
+        prog.specialise()
+    return prog
+
+
+ENGINES = pytest.mark.parametrize("spec", [False, True], ids=["table-driven", "specialised"])
+
+
+@ENGINES
+def test_fib22_all_modes(trs, spec):
+    """Single term fib(22), pool 2^24: plain, exact frontier (synchronous and
+    eager, one block for small frontiers), and the launch options the
+    benchmark times."""
+    t = ti.FIB
+    prog = program(trs, t, spec)
     want = Oracle(t).normalize(ti.fib_term(22))
     par = Oracle(t).normalize(ti.fib_term(22), "parallel")
     for kw in (dict(mode="plain"), dict(mode="frontier", solo_max=512),
-               dict(mode="frontier", solo_max=512, eager=64)):
+               dict(mode="frontier", solo_max=512, eager=64), trs.autotune_defaults("frontier", "fib22")):
         pool = trs.Pool(prog, 1 << 24)
         r = pool.term_upload(ti.fib_term(22))
         st = pool.trs_normalize(**kw)
+        assert st["specialised"] == int(spec)
         assert np.array_equal(pool.term_download(r), want.term), kw
         assert st["rewrites"] == 186579 and st["nf_marks"] == want.nf_marks
         if not kw.get("eager"):
             assert st["sweeps"] == par.sweeps == 35509
 
 
-def test_config4_uneven_fib_batch_graph(trs):
+@ENGINES
+def test_config4_uneven_fib_batch_graph(trs, spec):
     """10,000 terms fib(n), n uniform in [5, 20], pool 2^28, CUDA-graph loop."""
     t = ti.FIB
     flat, offs, ns = ti.fib_batch(seed=0, count=10000)
-    prog = trs.trs_compile(t)
+    prog = program(trs, t, spec)
     pool = trs.Pool(prog, 1 << 28)
     roots = pool.term_upload_batch(flat, offs)
     st = pool.trs_normalize(mode="frontier", driver="graph", graph_unroll=4, eager=256,
@@ -83,7 +97,8 @@ def test_config4_uneven_fib_batch_graph(trs):
         assert np.array_equal(got[i], o.normalize(flat[offs[i]:offs[i + 1]]).term)
 
 
-def test_config3_arith_trees_full(trs):
+@ENGINES
+def test_config3_arith_trees_full(trs, spec):
     """4096 balanced plus/times trees of depth 10..14, pool 2^28."""
     t = ti.ARITH
     flat, offs, meta = ti.arith_batch(seed=0, count=4096)
@@ -95,10 +110,10 @@ def test_config3_arith_trees_full(trs):
         assert np.array_equal(vals[h], np.where(ops[h] == 1, a * b, a + b))
         total += int(np.where(ops[h] == 1, a * (b + 2) + 1, a + 1).sum())
         values.append(int(vals[1]))
-    prog = trs.trs_compile(t)
+    prog = program(trs, t, spec)
     pool = trs.Pool(prog, 1 << 28)
     roots = pool.term_upload_batch(flat, offs)
-    st = pool.trs_normalize(mode="frontier", eager=256, solo_max=512)
+    st = pool.trs_normalize(mode="frontier", eager=1024 if spec else 256, solo_max=512)
     assert st["status"] == 0 and st["rewrites"] == total
     got = pool.term_download_batch(roots, cap=sum(values) + len(values))
     for g, v in zip(got, values):
@@ -111,7 +126,8 @@ def test_config3_arith_trees_full(trs):
         assert np.array_equal(got[i], r.term)
 
 
-def test_config5_merge_sort_full(trs):
+@ENGINES
+def test_config5_merge_sort_full(trs, spec):
     """256 lists of 64..1024 numerals 0..31 in a Node tree; every leaf sorted,
     rewrite count equal to the oracle's."""
     t = ti.MSORT
@@ -120,7 +136,7 @@ def test_config5_merge_sort_full(trs):
     expect = ti.msort_tree([sorted(l) for l in lists])
     expect = expect[expect != t.id["Sort"]]
     assert np.array_equal(want.term, expect)
-    prog = trs.trs_compile(t)
+    prog = program(trs, t, spec)
     for kw in (dict(mode="frontier", eager=256, solo_max=512), dict(mode="frontier")):
         pool = trs.Pool(prog, 1 << 24)
         r = pool.term_upload(term)
@@ -129,14 +145,15 @@ def test_config5_merge_sort_full(trs):
         assert st["rewrites"] == want.rewrites and st["nf_marks"] == want.nf_marks
 
 
-def test_ttree22_paper_headline(trs):
+@ENGINES
+def test_ttree22_paper_headline(trs, spec):
     """Transformation tree of depth 22 (Sec. 4 and appendix): Expand(Suc^22(Zero))
     becomes the complete Node tree with 2^22 End leaves after 28 * 2^22 - 1
     rewrites (2^23 - 1 Expand steps, 26 letter steps per leaf).  The plain
     sweep runs here over a store of several million slots with candidates in
     every sweep, the large-store form of its stamp scan."""
     t = ti.TTREE
-    prog = trs.trs_compile(t)
+    prog = program(trs, t, spec)
     n = 22
     expect = np.where(ti._heap_preorder(n) < (1 << n), t.id["Node"], t.id["End"]).astype(np.int32)
     for kw in (dict(mode="frontier", eager=64), dict(mode="frontier"), dict(mode="plain")):
