@@ -173,6 +173,54 @@ def test_parallel_sweeps_plus_closed_form():
             assert value(P, r.term) == a + b and r.rewrites == a + 1
 
 
+def test_parallel_sweeps_fib_closed_form():
+    """Sweeps of fib(S^n(0)) under synchronous parallel innermost.
+
+    Let a fib node be created in sweep t with an argument S^m(0) in normal
+    form, and let E(m) be the number of sweeps until its result is in normal
+    form (from sweep t + E(m) on).  fib(0) -> 0 fires in t+1 and the new 0 is
+    marked in t+2: E(0) = 3.  fib(S(0)) -> S(0) fires in t+1, 0 is marked in
+    t+2, S in t+3: E(1) = 4.  fib(S(S(x))) -> plus(fib(x), fib(S(x))) fires in
+    t+1; the new S(x) is marked in t+2, so fib(S(x)) acts as if created in
+    t+2 and ends last, at t+2+E(m-1); plus then peels F(m-2) S's, one per
+    sweep, plus(0,y) -> y is in normal form at once, and the F(m-2) new S
+    nodes above it are marked one per sweep (the plus closed form above):
+    E(m) = E(m-1) + 2F(m-2) + 3, so E(m) = 2F(m) + 3m - 1 for m >= 1.
+    The input numeral takes n+1 sweeps to become normal, so the last sweep
+    that acts is n + E(n): 2F(n) + 4n - 1 sweeps for n >= 1 (35,509 for
+    fib(22)), 3 for n = 0."""
+    o = Oracle(ti.FIB)
+    F = [0, 1]
+    for k in range(2, 30):
+        F.append(F[-1] + F[-2])
+    assert o.normalize(ti.fib_term(0), "parallel").sweeps == 3
+    for n in range(1, 17):
+        assert o.normalize(ti.fib_term(n), "parallel").sweeps == 2 * F[n] + 4 * n - 1, n
+    assert 2 * F[22] + 4 * 22 - 1 == 35509
+
+
+def test_fib_nf_marks_recurrence():
+    """Normal-form marks of fib(S^n(0)) (rewrites that leave a normal form at
+    once, plus(0,y) -> y, are not marks).  The input numeral takes n+1 marks.
+    For a fib node over a normal numeral S^m(0), N(m) marks: fib(0) -> 0 leaves
+    one new 0 to mark, N(0) = 1; fib(S(0)) -> S(0) leaves 0 and S, N(1) = 2;
+    fib(S(S(x))) -> plus(fib(x), fib(S(x))) leaves the new S(x) (one mark), the
+    two fib nodes (N(m-2) + N(m-1)), and plus peels the F(m-2) S nodes of its
+    first argument into new S nodes that are marked once its copy of the
+    second argument is in place: N(m) = N(m-1) + N(m-2) + F(m-2) + 1.
+    fib(22): 175,657 marks."""
+    o = Oracle(ti.FIB)
+    F = [0, 1]
+    for k in range(2, 30):
+        F.append(F[-1] + F[-2])
+    N = [1, 2]
+    for m in range(2, 23):
+        N.append(N[-1] + N[-2] + F[m - 2] + 1)
+    for n in range(0, 17):
+        assert o.normalize(ti.fib_term(n)).nf_marks == n + 1 + N[n], n
+    assert 22 + 1 + N[22] == 175657
+
+
 def test_parallel_sweeps_ttree_closed_form():
     """Expand(Suc^N(Zero)): N+1 sweeps make the numeral normal, N sweeps expand
     one level each, one sweep turns every Expand(Zero) into A, 26 sweeps walk
