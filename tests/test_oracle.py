@@ -123,11 +123,14 @@ def test_nonterminating_hits_step_cap():
 def test_transformation_tree_leaf_rewrites():
     """Sec. 4: each of the 2^N leaves is rewritten 26 times; with the 2^(N+1)-1
     Expand/Expand2 steps the total is 28*2^N - 1; the result is a complete Node
-    tree with End leaves."""
+    tree with End leaves.  Normal-form marks: the N+1 nodes of the input
+    numeral (shared by Expand and Expand2, so marked once each), every End leaf
+    and every Node: N + 2^(N+1)."""
     o = Oracle(ti.TTREE)
     for n in range(0, 9):
         r = o.normalize(ti.ttree_term(n))
         assert r.rewrites == 28 * 2 ** n - 1
+        assert r.nf_marks == n + 2 ** (n + 1)
         assert r.rule_counts[4:].sum() == 26 * 2 ** n
         assert len(r.term) == 2 ** (n + 1) - 1
         leaves = [x for x in r.term if x != ti.TTREE.id["Node"]]
