@@ -247,6 +247,21 @@ def _arith_expect(meta):
     return int(vals[1]), cost
 
 
+def _arith_marks(meta):
+    """Normal-form marks of an arithmetic tree under innermost rewriting: each
+    leaf numeral S^v(0) takes v+1; plus(S^a(0), y) leaves a new S nodes to mark
+    (plus(0,y) -> y is a normal form at once); times(S^a(0), S^b(0)) leaves
+    the 0 of times(0,y) -> 0 and the a*b S nodes its a plus(y, .) steps peel
+    from y."""
+    depth, ops, vals = meta
+    nl = 1 << depth
+    marks = int(sum(int(vals[h]) + 1 for h in range(nl, 2 * nl)))
+    for h in range(1, nl):
+        a, b = int(vals[2 * h]), int(vals[2 * h + 1])
+        marks += a * b + 1 if ops[h] else a
+    return marks
+
+
 @pytest.mark.parametrize("mode", ["innermost", "parallel", "outermost"])
 def test_arith_trees_closed_form(mode):
     flat, offs, meta = ti.arith_batch(seed=3, count=12, dmin=1, dmax=5)
@@ -257,6 +272,7 @@ def test_arith_trees_closed_form(mode):
         assert value(ti.ARITH, r.term) == v
         if mode != "outermost":
             assert r.rewrites == cost
+            assert r.nf_marks == _arith_marks(m)
 
 
 @pytest.mark.parametrize("mode", ["innermost", "parallel"])
