@@ -224,6 +224,34 @@ def test_fib_nf_marks_recurrence():
     assert 22 + 1 + N[22] == 175657
 
 
+def test_msort_equal_values_recurrence():
+    """Rewrites of Leaf(Sort(L)) for a list of k equal numerals S^v(0), from the
+    appendix rules: Sort -> Sort2(Gt(Len(L), S(Zero)), L) (1), Len (k+1),
+    Gt (1 for k = 0, else 2), Sort2 (1); for k <= 1 that is all (4 and 6).
+    For k >= 2 Sort2 -> Merge(Sort(Even(L)), Sort(Odd(L))), Even and Odd take
+    k+1 each, the halves have ceil(k/2) and floor(k/2) elements, and merging
+    q = floor(k/2) elements in from the right takes per element Merge ->
+    Merge2 (1), Lt(S^v, S^v) (v+1) and Merge2(False, ...) (1), then one
+    Merge(L, Nil) -> L:
+    R(k) = 3k + 8 + (3 + v) q + R(ceil(k/2)) + R(floor(k/2)).
+    Lists in the leaves of one Node tree add up (Node and Leaf have no rules)."""
+    o = Oracle(ti.MSORT)
+
+    def R(k, v):
+        if k <= 1:
+            return 4 if k == 0 else 6
+        q = k // 2
+        return 3 * k + 8 + (3 + v) * q + R(k - q, v) + R(q, v)
+
+    for v in (0, 1, 4):
+        for k in range(0, 21):
+            r = o.normalize(ti.msort_tree([[v] * k]))
+            assert r.rewrites == R(k, v), (v, k)
+    lists = [[2] * 5, [0] * 9, [3] * 1, [1] * 12]
+    r = o.normalize(ti.msort_tree(lists))
+    assert r.rewrites == sum(R(len(x), x[0] if x else 0) for x in lists)
+
+
 def test_parallel_sweeps_ttree_closed_form():
     """Expand(Suc^N(Zero)): N+1 sweeps make the numeral normal, N sweeps expand
     one level each, one sweep turns every Expand(Zero) into A, 26 sweeps walk
