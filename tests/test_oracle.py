@@ -176,6 +176,27 @@ def test_parallel_sweeps_plus_closed_form():
             assert value(P, r.term) == a + b and r.rewrites == a + 1
 
 
+def test_parallel_sweeps_times_closed_form():
+    """Sweeps of times(S^a(0), S^b(0)) under synchronous parallel innermost.
+    The numerals are normal after max(a,b)+1 sweeps and times is ready in the
+    next.  Let T(a) count the sweeps from the one in which a times node over
+    S^a(0) and S^b(0) is ready to the first in which its result is normal:
+    times(0,y) -> 0 fires, then the new 0 is marked, T(0) = 2; times(S(x),y)
+    -> plus(y, times(x,y)) fires, the new times node is ready one sweep later
+    and takes T(a-1), then plus(S^b(0), .) peels b S's, copies its second
+    argument and marks the b new S nodes (2b+1 sweeps, the plus closed form):
+    T(a) = T(a-1) + 2b + 2.  The last sweep that acts is max(a,b) + 3 +
+    2a(b+1)."""
+    o = Oracle(ti.ARITH)
+    P = ti.ARITH
+    for a in range(0, 8):
+        for b in range(0, 8):
+            t = np.concatenate([[P.id["times"]], ti.peano(P, a), ti.peano(P, b)])
+            r = o.normalize(t, "parallel")
+            assert r.sweeps == max(a, b) + 3 + 2 * a * (b + 1), (a, b)
+            assert value(P, r.term) == a * b and r.rewrites == a * (b + 2) + 1
+
+
 def test_parallel_sweeps_fib_closed_form():
     """Sweeps of fib(S^n(0)) under synchronous parallel innermost.
 
