@@ -311,6 +311,24 @@ def _arith_marks(meta):
     return marks
 
 
+def _arith_sweeps(meta):
+    """Parallel-innermost sweeps of an arithmetic tree: a leaf S^v(0) is normal
+    from sweep v+2; an operator is ready once both arguments are normal and
+    then takes the times and plus closed forms below (2a+1 sweeps for plus,
+    2 + 2a(b+1) for times) until its result is normal; the count is the last
+    sweep that acts."""
+    depth, ops, vals = meta
+    nl = 1 << depth
+    vis = [0] * (2 * nl)
+    for h in range(nl, 2 * nl):
+        vis[h] = int(vals[h]) + 2
+    for h in range(nl - 1, 0, -1):
+        a, b = int(vals[2 * h]), int(vals[2 * h + 1])
+        ready = max(vis[2 * h], vis[2 * h + 1])
+        vis[h] = ready + 2 + 2 * a * (b + 1) if ops[h] else ready + 2 * a + 1
+    return vis[1] - 1
+
+
 @pytest.mark.parametrize("mode", ["innermost", "parallel", "outermost"])
 def test_arith_trees_closed_form(mode):
     flat, offs, meta = ti.arith_batch(seed=3, count=12, dmin=1, dmax=5)
@@ -322,6 +340,8 @@ def test_arith_trees_closed_form(mode):
         if mode != "outermost":
             assert r.rewrites == cost
             assert r.nf_marks == _arith_marks(m)
+        if mode == "parallel":
+            assert r.sweeps == _arith_sweeps(m)
 
 
 @pytest.mark.parametrize("mode", ["innermost", "parallel"])
