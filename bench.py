@@ -1,18 +1,31 @@
 #!/usr/bin/env python
-"""Benchmark of the term-rewriting engine: node-rewrites/s on Peano fib(22).
+"""Benchmark of the term-rewriting engine: node-rewrites/s on the five synthetic
+workloads of the method, headline on the largest one.
 
-Workload: one term fib(S^22(0)) in a node pool of 2^24 slots, normalised to
-S^17711(0) (186,579 rewrites).  A step is one normalisation of that term
-through the C ABI; the term is uploaded before each step's timed region
-(inputs resident in HBM), and L2 is flushed between steps.  The headline
-engine (exact frontier with eager continuation, autotuned options) runs next
-to the plain all-node sweep (the paper's topology-driven derive kernel) and
-the learned frontier, whose predictor is trained on the engine's own traces
-of smaller Fibonacci terms before anything is timed.
+Headline workload: 4,096 seeded arithmetic trees (balanced plus/times trees of
+depth 10..14 over Peano numerals 0..8, 158.5M input nodes) normalised in one
+batched persistent launch in a pool of 2^29 node slots, 30 GB of the GPU's
+HBM (726,705,404 rewrites).
+A step is one normalisation of the whole batch through the C ABI with the
+inputs resident in HBM (uploaded before the timed region; the input store,
+about 5 GB of node records, is far larger than L2).  `e2e` times the same step
+through the public API with host buffers: upload of the preorder terms,
+normalisation, download of every normal form.
+
+Beside it, one block per workload (Peano fib(15); fib(22) in a 2^24 pool; the
+4,096 trees; 10,000 fib(n) terms, n uniform in [5, 20], in a 2^28 pool on the
+CUDA-graph driver; merge sort of 256 lists; the transformation tree of depth
+22) gives the time to normal form and node-rewrites/s of the exact frontier
+(the tuned engine), the plain all-node sweep (the paper's topology-driven
+derive kernel), the learned frontier (predictor trained first on the engine's
+own traces of smaller terms of the same rule system) and the CPU oracle on
+the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-For N > 1 (torchrun, one rank per GPU) every rank normalises its own replica
-of the term (a single term does not shard: replicas only).
+       python bench.py --case NAME   (one small normalisation for a profiler)
+With N > 1 (torchrun, one rank per GPU) the job is N x 4,096 trees, partitioned
+across the ranks by estimated cost (each rank about one 4,096-tree batch, no
+exchange while rewriting): weak scaling.
 """
 import argparse
 import json
@@ -21,6 +34,7 @@ import re
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -32,9 +46,66 @@ import trs_inputs as ti  # noqa: E402
 
 METRIC = "node-rewrites/sec and time-to-normal-form vs plain sweep; % HBM roofline"
 UNIT = "node-rewrites/s"
-WORKLOAD = "peano fib(22) single term, node pool 2^24 int32 slots"
-POOL = 1 << 24
-FIB_N = 22
+HEAD = "c3"
+
+
+def fib_numbers(n):
+    a, b = 0, 1
+    for _ in range(n):
+        a, b = b, a + b
+    return a
+
+
+def fib_rewrites(n):
+    """T(0) = T(1) = 1, T(n) = T(n-1) + T(n-2) + F(n-2) + 2 (rewrites of fib(n))."""
+    T = [1, 1]
+    for k in range(2, n + 1):
+        T.append(T[k - 1] + T[k - 2] + fib_numbers(k - 2) + 2)
+    return T[n]
+
+
+def arith_rewrites(meta):
+    """Sum over the trees' inner nodes of a + 1 (plus) and a(b + 2) + 1 (times)."""
+    tot = 0
+    for d, ops, vals in meta:
+        h = np.arange(1, 1 << d)
+        a, b = vals[2 * h], vals[2 * h + 1]
+        tot += int(np.where(ops[h] == 1, a * (b + 2) + 1, a + 1).sum())
+    return tot
+
+
+def build_workload(name, seed=0):
+    """(trs, flat, offsets, pool capacity, expected rewrites or None, description,
+    autotune workload key, terms for the oracle sample)."""
+    if name == "c1":
+        f, o = ti.concat_terms([ti.fib_term(15)])
+        return ti.FIB, f, o, 1 << 20, 5244, "Peano fib(15), single term, pool 2^20", "fib22"
+    if name == "c2":
+        f, o = ti.concat_terms([ti.fib_term(22)])
+        return ti.FIB, f, o, 1 << 24, 186579, "Peano fib(22), single term, pool 2^24", "fib22"
+    if name == "c3":
+        f, o, meta = ti.arith_batch(seed=seed, count=4096)
+        return (ti.ARITH, f, o, 1 << 29, arith_rewrites(meta),
+                "4096 arithmetic trees (plus/times, depth 10..14, numerals 0..8), pool 2^29", "arith-4096")
+    if name == "c4":
+        f, o, ns = ti.fib_batch(seed=seed, count=10000)
+        return (ti.FIB, f, o, 1 << 28, sum(fib_rewrites(int(n)) for n in ns),
+                "10000 fib(n), n uniform in [5, 20], pool 2^28, CUDA-graph driver", "fib-batch-10000")
+    if name == "c5":
+        term, _ = ti.msort_batch(seed=seed)
+        f, o = ti.concat_terms([term])
+        return (ti.MSORT, f, o, 1 << 24, None,
+                "merge sort of 256 lists (64..1024 numerals 0..31), single term, pool 2^24", "msort")
+    if name == "ttree22":
+        f, o = ti.concat_terms([ti.ttree_term(22)])
+        return (ti.TTREE, f, o, 1 << 24, 28 * 2 ** 22 - 1,
+                "transformation tree Expand(Suc^22(Zero)), single term, pool 2^24", "ttree")
+    raise KeyError(name)
+
+
+CONFIGS = ["c1", "c2", "c3", "c4", "c5", "ttree22"]
+# launch options beyond the tuned ones (config 4 runs on the CUDA-graph driver)
+EXTRA = {"c4": {"driver": "graph", "graph_unroll": 4, "solo_max": 0}}
 
 
 def peaks():
@@ -65,6 +136,16 @@ def reduce_max(x):
         return x
     t = torch.tensor([float(x)], device="cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x):
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        return x
+    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t)
     return float(t.item())
 
 
@@ -146,7 +227,6 @@ def profiled_traffic(name, units=None):
     for line in open(path):
         if "=" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split("=", 1)
-            # the value is the first `quoted` token (a remark may follow it)
             m = re.search(r"`([^`]*)`", v)
             vals[k.strip().strip("`")] = m.group(1) if m else v.strip()
     if vals.get("source_sha256") != kernel_source_hash():
@@ -160,243 +240,354 @@ def profiled_traffic(name, units=None):
         return None
 
 
-def alg_bytes(st, trace, ma):
+def alg_bytes(st, trace, ma, mode):
     """Algorithmic bytes of one normalisation (the byte model of the design
     notes): the all-slot stamp scans, the per-node reads of visited nodes and
-    their arguments' stamps, the writes of rewrites and new nodes, and the
-    garbage-collection and seed scans."""
+    their arguments' stamps, the writes of rewrites and new nodes, the
+    collections (per node freed) and the seed / confirmation scans."""
     node = 4 + 4 * ma                     # head + argument indices
     b = 0
-    if trace:
-        b += sum(r[5] for r in trace) * 4 if st["mode"] == "plain" else 0
+    if mode == "plain" and trace:
+        b += sum(r[5] for r in trace) * 4            # stamp stream of every sweep
     b += st["visits"] * (node + 4 * ma + 4)          # node, argument stamps, own stamp
     b += st["rewrites"] * (node + 2 * 8 + 3 * 4)     # write node, ~2 pattern gathers, ~3 count atomics
     b += st["allocs"] * (node + 16)                  # new node: head, args, count, stamp, parent, pending
     b += st["nf_marks"] * 8                          # stamp write, parent's pending count
-    b += st["gc_runs"] * st["high_water"] * 8 + st["frees"] * (node + 4)
-    b += (st["confirm_sweeps"] + (1 if st["mode"] != "plain" else 0)) * st["high_water"] * 4
-    if st["mode"] != "plain":
+    b += st["frees"] * (4 + node + 4 + 4)            # dead-list entry, record, stamp, ring entry
+    b += (st["confirm_sweeps"] + (1 if mode != "plain" else 0)) * st["high_water"] * 4
+    if mode != "plain":
         b += st["visits"] * 8                        # frontier entry read + push
     return b
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+
+class Runner:
+    """One workload on this GPU: program (specialised), pool, timed runs."""
+
+    def __init__(self, name, seed=0, pool=None, flat=None, offs=None):
+        import paper_2009_07174_gb300 as trs
+        self.trs = trs
+        self.name = name
+        (self.t, f, o, self.cap, self.expect, self.desc, self.tune_key) = build_workload(name, seed)
+        self.flat, self.offs = (f, o) if flat is None else (flat, offs)
+        self.prog = trs.trs_compile(self.t)
+        self.pool = pool
+
+    def specialise(self):
+        t0 = time.perf_counter()
+        self.prog.specialise()
+        return time.perf_counter() - t0
+
+    def opts(self, mode):
+        from paper_2009_07174_gb300 import autotune_defaults
+        kw = autotune_defaults(mode, self.tune_key)
+        if mode == "frontier":
+            kw.update(EXTRA.get(self.name, {}))
+        return kw
+
+    def ensure_pool(self):
+        if self.pool is None:
+            self.pool = self.trs.Pool(self.prog, self.cap)
+        return self.pool
+
+    def run(self, kw, trace=0):
+        """Reset, upload (untimed), normalise (CUDA events on the launching
+        stream).  Returns (ms, stats, roots)."""
+        import torch
+        pool = self.ensure_pool()
+        pool.trs_pool_reset()
+        roots = pool.term_upload_batch(self.flat, self.offs)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        try:
+            pool.trs_normalize(wait=False, trace=trace, **kw)
+        finally:
+            e1.record(stream)
+        e1.synchronize()
+        try:
+            st = pool.trs_pool_stats()
+        except self.trs.TrsError as e:
+            st = {"status": e.name}
+        return e0.elapsed_time(e1), st, roots
+
+    def check(self, st):
+        ok = st.get("status") == 0
+        if ok and self.expect is not None:
+            ok = st["rewrites"] == self.expect
+        return ok
+
+    def free(self):
+        self.pool = None
+
+
+def time_mode(r, kw, reps):
+    times, st = [], None
+    for _ in range(reps):
+        ms, st, _ = r.run(kw)
+        if not r.check(st):
+            return {"status": st.get("status"), "opts": kw, "stats": st}
+        times.append(ms)
+    ms = statistics.mean(times)
+    return {"ms": ms, "value": st["rewrites"] / (ms / 1e3), "opts": kw,
+            "sweeps": st["sweeps"], "visits": st["visits"], "gc_runs": st["gc_runs"],
+            "frees": st["frees"], "high_water": st["high_water"], "solo_sweeps": st["solo_sweeps"],
+            "refreshes": st["refreshes"], "rewrites": st["rewrites"]}
+
+
+def plain_sampled(r, sweeps):
+    """The plain sweep over the first `sweeps` sweeps only (a full run would
+    take minutes): rewrites/s over that prefix, which holds the widest
+    sweeps (the plain sweep's most favourable part)."""
+    import ctypes
+    kw = dict(r.opts("plain"), max_sweeps=sweeps)
+    ms, st, _ = r.run(kw)
+    if st.get("status") not in ("TRS_ERR_SWEEP_LIMIT", 0):
+        return {"status": st.get("status")}
+    # the counters of the run the sweep limit stopped
+    S = r.trs.Stats()
+    r.trs.lib.trs_pool_stats(r.pool._h, ctypes.byref(S), r.trs._stream())
+    s = S.as_dict()
+    return {"ms": ms, "value": s["rewrites"] / (ms / 1e3), "sampled_sweeps": s["sweeps"],
+            "rewrites": s["rewrites"], "note": f"first {sweeps} sweeps only (rewrites/s over them)"}
+
+
+def train_predictor(name):
+    """Predictor of the learned frontier for the rule system of `name`, trained
+    on the engine's own traces of a smaller workload of that system."""
+    import paper_2009_07174_gb300 as trs
+    from paper_2009_07174_gb300 import learn
+    if name in ("c1", "c2", "c4"):
+        t, terms, cap = ti.FIB, [ti.fib_term(n) for n in range(8, 21)], 1 << 24
+    elif name == "c3":
+        f, o, _ = ti.arith_batch(seed=7, count=64, dmin=10, dmax=11)
+        t, terms, cap = ti.ARITH, [f[o[i]:o[i + 1]] for i in range(64)], 1 << 24
+    elif name == "c5":
+        t, terms, cap = ti.MSORT, [ti.msort_batch(seed=7, nlists=16, lmin=64, lmax=256)[0]], 1 << 22
+    else:
+        t, terms, cap = ti.TTREE, [ti.ttree_term(14)], 1 << 22
+    prog = trs.trs_compile(t)
+    prog.specialise()
+    flat, offs = ti.concat_terms(terms)
+    pred, info = learn.train_for(prog, flat, offs, cap, period=16, return_info=True)
+    return prog, pred, info
+
+
+def config_block(name, spec_s, budget_s=60.0):
+    """Exact frontier, plain sweep, learned frontier of one workload."""
+    import torch
+    r = Runner(name)
+    r.prog.specialise()
+    out = {"workload": r.desc, "specialise_s": spec_s.get(r.t.name)}
+    big = r.cap >= (1 << 28)
+    out["frontier"] = time_mode(r, r.opts("frontier"), 2 if big else 3)
+    out["rewrites"] = out["frontier"].get("rewrites")
+    if name == "c3":
+        out["plain_sweep"] = plain_sampled(r, 40)
+    else:
+        out["plain_sweep"] = time_mode(r, r.opts("plain"), 1)
+    # learned frontier: predictor trained on smaller terms of the same rules
+    t0 = time.perf_counter()
+    prog, pred, info = train_predictor(name)
+    r.prog = prog
+    r.pool = None
+    r.ensure_pool().trs_pool_attach_predictor(pred)
+    kw = dict(r.opts("learned"), time_limit_ns=int(budget_s * 1e9))
+    learned = time_mode(r, kw, 1)
+    learned["train_s"] = time.perf_counter() - t0
+    learned["train_rows"] = info["rows"]
+    out["learned_frontier"] = learned
+    f = out["frontier"]
+    for k in ("plain_sweep", "learned_frontier"):
+        if "ms" in out[k] and "ms" in f and "sampled_sweeps" not in out[k]:
+            out[k]["frontier_speedup"] = out[k]["ms"] / f["ms"]
+    r.free()
+    torch.cuda.empty_cache()
+    return out
+
+
+def specialise_all():
+    """Compile the specialised engines of every rule system in parallel
+    threads (NVRTC; the C calls release the GIL)."""
+    import paper_2009_07174_gb300 as trs
+    res = {}
+
+    def one(t):
+        t0 = time.perf_counter()
+        trs.trs_compile(t).specialise()
+        res[t.name] = time.perf_counter() - t0
+
+    th = [threading.Thread(target=one, args=(t,)) for t in (ti.FIB, ti.ARITH, ti.MSORT, ti.TTREE)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    return res
 
 
 def run_ours(args, rank, ws, local):
     import torch
     import paper_2009_07174_gb300 as trs
-    from paper_2009_07174_gb300 import autotune_defaults, learn
+    from paper_2009_07174_gb300 import shard
 
     torch.cuda.set_device(local)
-    term = ti.fib_term(FIB_N)
-    prog = trs.trs_compile(ti.FIB)
-    # the engine specialised to the rule system (generated rule code, compiled
-    # at run time and cached); compiled before anything is timed
-    t_spec = time.perf_counter()
-    prog.specialise()
-    spec_s = time.perf_counter() - t_spec
-    pool = trs.Pool(prog, POOL)
+    spec_s = specialise_all()
+    # the headline batch: with N ranks, N x 4096 trees partitioned by cost
+    if ws == 1:
+        head = Runner(HEAD)
+    else:
+        f, o, meta = ti.arith_batch(seed=0, count=4096 * ws)
+        idx = shard.partition(shard.arith_costs(meta), ws)[rank]
+        lf, lo = shard.local_batch(f, o, idx)
+        head = Runner(HEAD, flat=lf, offs=lo)
+        head.expect = arith_rewrites([meta[i] for i in idx])
+    head.prog.specialise()
+    head.ensure_pool()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def one(kw, trace=0):
-        pool.trs_pool_reset()
-        root = pool.term_upload(term)
-        flush.fill_(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pool.trs_normalize(wait=False, trace=trace, **kw)
-        e1.record(stream)
-        return root, e0, e1
-
-    def timed(kw, steps, warmup, clocks=None):
-        for _ in range(warmup):
-            root, e0, e1 = one(kw)
-        st = pool.trs_pool_stats()
-        res = pool.term_download(root)
-        assert len(res) == 17712 and st["rewrites"] == 186579, st
-        torch.cuda.synchronize()
-        times = []
-        for _ in range(steps):
-            root, e0, e1 = one(kw)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        return sum(times) / len(times), pool.trs_pool_stats()
-
-    # the predictor of the learned frontier, trained on the engine's own traces
-    # of smaller Fibonacci terms before anything is timed
-    flat, offs = ti.concat_terms([ti.fib_term(n) for n in range(8, 21)])
-    pred, info = learn.train_for(prog, flat, offs, 1 << 24, period=16, return_info=True)
-    pool.trs_pool_attach_predictor(pred)
-
-    head_kw = autotune_defaults(args.mode, "fib22")
+    kw = head.opts("frontier")
+    for _ in range(args.warmup):
+        ms, st, _ = head.run(kw)
+        assert head.check(st), st
     barrier()
     torch.cuda.synchronize()
+    times = []
     with Clocks(local) as clk:
-        ms, st = timed(head_kw, args.steps, args.warmup)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ms, st, _ = head.run(kw)
+            assert head.check(st), st
+            times.append(ms)
         torch.cuda.synchronize()
     barrier()
+    ms = statistics.mean(times)
     ms_max = reduce_max(ms)
-    rewrites = st["rewrites"]
-    value = rewrites * ws / (ms_max / 1e3)
+    rewrites_all = reduce_sum(st["rewrites"])
+    value = rewrites_all / (ms_max / 1e3)
 
-    # roofline of the engine kernel (one launch per step) with the per-sweep trace
-    root, e0, e1 = one(head_kw, trace=1)
-    torch.cuda.synchronize()
-    tr = pool.trs_trace_read()
-    st_tr = pool.trs_pool_stats()
-    st_tr["mode"] = head_kw["mode"]
-    nbytes = alg_bytes(st_tr, tr, prog.maxarity)
+    # roofline of the engine kernel (one launch per step)
+    _, st_tr, _ = head.run(kw, trace=1)
+    tr = head.pool.trs_trace_read()
+    nbytes = alg_bytes(st_tr, tr, head.prog.maxarity, kw["mode"])
     peak, peak_kind = peaks()
     achieved = nbytes / (ms / 1e3) / 1e9
 
-    # the same step on the table-driven engine (rules interpreted from tables)
-    generic_ms, generic_st = timed(dict(head_kw, generic=1), 3, 1)
-    assert generic_st["specialised"] == 0 and st["specialised"] == 1
-
-    # the plain all-node sweep (the method without a frontier) and the learned frontier
-    plain_ms, plain_st = timed(autotune_defaults("plain", "fib22"), 2, 1)
-    learned_kw = autotune_defaults("learned", "fib22")
-    learned_ms, learned_st = timed(learned_kw, 3, 1)
-
-    scan = plain_scan_roofline()
-
-    # end to end through the C ABI with host buffers: upload, normalise, download
-    e2e_times = []
-    h2d = d2h = 0
-    for _ in range(args.steps):
+    # end to end through the C ABI with host buffers: upload of the preorder
+    # terms from pinned host memory, normalisation, download of every normal form
+    flat_pin = torch.from_numpy(np.ascontiguousarray(head.flat, dtype=np.int32)).pin_memory()
+    offs_pin = torch.from_numpy(np.ascontiguousarray(head.offs, dtype=np.int64)).pin_memory()
+    fl, of = flat_pin.numpy(), offs_pin.numpy()
+    e2e_times, out_syms = [], 0
+    for _ in range(max(2, min(args.steps, 4))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pool.trs_pool_reset()
-        r = pool.term_upload(term)
-        pool.trs_normalize(**head_kw)
-        out = pool.term_download(r)
+        head.pool.trs_pool_reset()
+        roots = head.pool.term_upload_batch(fl, of)
+        head.pool.trs_normalize(**kw)
+        res = head.pool.term_download_batch(roots, cap=1 << 28)
         t1 = time.perf_counter()
         e2e_times.append(t1 - t0)
-        # node records (rs words) and stamps of the term, the new high-water
-        # mark; the root's stamp and count, then every record below the mark
-        rs = 8 if prog.maxarity + 4 <= 8 else 16
-        h2d = len(term) * 4 * (rs + 1) + 8
-        d2h = 8 + st["high_water"] * 4 * rs
-        assert len(out) == 17712
-    e2e = rewrites * ws / reduce_max(statistics.mean(e2e_times))
+        out_syms = sum(len(x) for x in res)
+    h2d = fl.nbytes + of.nbytes
+    d2h = out_syms * 4 + (len(roots) + 1) * 8
+    e2e = rewrites_all / reduce_max(statistics.mean(e2e_times))
+    head.free()
+    del flush
+    torch.cuda.empty_cache()
 
+    blocks = {}
+    if rank == 0 and not args.headline_only:
+        for name in CONFIGS:
+            blocks[name] = config_block(name, spec_s)
     return {
-        "value": value, "ms": ms_max, "stats": st, "mode": head_kw["mode"], "opts": head_kw,
+        "value": value, "ms": ms_max, "stats": st, "opts": kw, "desc": head.desc,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic("k_engine_fib22_frontier"),
-                     "peak_kind": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": nbytes},
-        "plain": {"ms": plain_ms, "value": rewrites / (plain_ms / 1e3),
-                  "sweeps": plain_st["sweeps"], "visits": plain_st["visits"]},
-        "learned": {"ms": learned_ms, "value": rewrites / (learned_ms / 1e3), "opts": learned_kw,
-                    "sweeps": learned_st["sweeps"], "visits": learned_st["visits"],
-                    "refreshes": learned_st["refreshes"], "train_rows": info["rows"],
-                    "train_loss": [round(info["losses"][0], 4), round(info["losses"][-1], 4)]},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "plain_scan": scan,
-        "table_driven": {"ms": generic_ms, "value": rewrites / (generic_ms / 1e3)},
+                     "frac": achieved / peak, "traffic": profiled_traffic("k_engine_arith4096_frontier"),
+                     "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nbytes},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms": statistics.mean(e2e_times) * 1e3},
+        "clocks": clk.summary(), "gpu_launches": 2 * args.steps, "configs": blocks,
         "specialise_s": spec_s,
-        "clocks": clk.summary(),
-        "gpu_launches": 2 * args.steps,
     }
 
 
-def plain_scan_roofline(reps=5):
-    """HBM side of the plain sweep: a store of 2048 arithmetic trees already in
-    normal form (a high-water mark of over 10^8 slots, stamps far larger
-    than L2); one plain normalisation is then a single sweep that streams every
-    stamp and finds nothing to do.  Bytes = 4 per slot below the mark."""
-    import torch
-    import paper_2009_07174_gb300 as trs
-    from paper_2009_07174_gb300 import autotune
-    t, build, cap = autotune.workloads()["arith-2048"]
-    flat, offs = build()
-    prog = trs.trs_compile(t)
-    pool = trs.Pool(prog, cap)
-    pool.term_upload_batch(flat, offs)
-    pool.trs_normalize(mode="frontier", eager=64)
-    n = pool.trs_pool_stats()["high_water"]
-    times = []
-    for r in range(reps + 1):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        pool.trs_normalize(wait=False, mode="plain")
-        e1.record()
-        e1.synchronize()
-        if r:
-            times.append(e0.elapsed_time(e1))
-    st = pool.trs_pool_stats()
-    assert st["rewrites"] == 0 and st["sweeps"] == 0
-    ms = statistics.median(times)
-    peak, kind = peaks()
-    gbs = n * 4 / (ms / 1e3) / 1e9
-    del pool
-    return {"slots": n, "ms": ms, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "peak_kind": f"{kind} hbm_gbs", "workload": "2048 arithmetic trees in normal form, pool 2^28",
-            "traffic": profiled_traffic("k_engine_plain_scan", units=n)}
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline): leftmost-innermost C
+# rewriter on pointer trees, independent terms on host threads
 
-
-def cpu_baseline(target_s=10.0):
-    from oracle import Oracle
-    o = Oracle(ti.FIB)
-    term = ti.fib_term(FIB_N)
-    n, t0 = 0, time.perf_counter()
-    rew = 0
-    while time.perf_counter() - t0 < target_s:
-        r = o.normalize(term)
-        rew += r.rewrites
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": rew / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full normalisations of fib(22) (single-thread leftmost-innermost C oracle)",
-            "seconds": dt}
+def oracle_sample(name, target_s, threads=None):
+    """Rewrites/s of the oracle on a bounded sample of workload `name`."""
+    from oracle import Oracle, normalize_threads
+    threads = threads or os.cpu_count() or 1
+    t, flat, offs, _, _, _, _ = build_workload(name)
+    nterms = len(offs) - 1
+    terms = [flat[offs[i]:offs[i + 1]] for i in range(nterms)]
+    if nterms == 1:
+        o = Oracle(t)
+        n, rew, t0 = 0, 0, time.perf_counter()
+        while True:
+            rew += o.normalize(terms[0]).rewrites
+            n += 1
+            if time.perf_counter() - t0 >= target_s:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": rew / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{n} full normalisation(s) of the single term (1 thread)", "seconds": dt}
+    rng = np.random.default_rng(1)
+    order = rng.permutation(nterms)
+    done, rew, t0, used = 0, 0, time.perf_counter(), 0
+    step = max(threads * 4, 64)
+    while done < nterms:
+        part = [terms[i] for i in order[done:done + step]]
+        res = normalize_threads(t, part, threads)
+        rew += sum(r.rewrites for r in res)
+        done += len(part)
+        used = time.perf_counter() - t0
+        if used >= target_s:
+            break
+    return {"value": rew / used, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done} of {nterms} terms (seeded random order), {threads} host threads",
+            "seconds": used}
 
 
 PROFILE_CASES = {
-    # name: (workload, pool capacity, launch options) -- single normalisations
-    # for profilers (a few GB on the device at most)
-    "fib22-frontier": ("fib22", 1 << 24, None),
-    "fib22-plain": ("fib22", 1 << 24, {"mode": "plain"}),
-    "fib-batch-frontier": ("fib-batch", 1 << 26, None),
-    "fib-batch-plain": ("fib-batch", 1 << 26, {"mode": "plain", "max_sweeps": 64}),
-    "arith-frontier": ("arith", 1 << 26, None),
-    "ttree-frontier": ("ttree", 1 << 24, None),
-    # a store already in normal form: the plain sweep is one streaming scan
-    # (table-driven, so that the store it scans, built without slot reuse, is
-    # larger than L2)
-    "arith-plain-scan": ("arith-768", 1 << 26, {"mode": "plain", "generic": 1}),
-    # the full-size batches (pool 2^28, about 7 GB): single-pass counters only
-    "arith-4096-frontier": ("arith-4096", 1 << 28, {"mode": "frontier", "eager": 256, "solo_max": 512}),
-    "fib-batch-10000-frontier": ("fib-batch-10000", 1 << 28, {"mode": "frontier", "eager": 64,
-                                                              "block_size": 256}),
+    # name: (workload, launch options) -- one normalisation for a profiler; a
+    # few GB on the device at most
+    "fib22-frontier": ("c2", None),
+    "fib22-plain": ("c2", {"mode": "plain"}),
+    "arith512-frontier": ("arith-512", None),
+    "fib-batch2000-frontier": ("fib-batch-2000", None),
+    "msort-frontier": ("c5", None),
+    "ttree20-frontier": ("ttree20", None),
 }
-PRE_NORMALISE = {"arith-plain-scan": {"mode": "frontier", "eager": 64, "generic": 1}}
 
 
 def run_case(name, reps):
-    """One case of PROFILE_CASES, `reps` times (exit status 0 also when a
-    plain case stops at its sweep limit on purpose)."""
     import torch
     import paper_2009_07174_gb300 as trs
-    from paper_2009_07174_gb300 import autotune, autotune_defaults
-    wl, cap, kw = PROFILE_CASES[name]
-    t, build, _ = autotune.workloads()[wl]
-    flat, offs = build()
+    from paper_2009_07174_gb300 import autotune_defaults
+    wl, kw = PROFILE_CASES[name]
+    if wl == "arith-512":
+        f, o, _ = ti.arith_batch(seed=0, count=512)
+        t, cap, key = ti.ARITH, 1 << 26, "arith-4096"
+    elif wl == "fib-batch-2000":
+        f, o, _ = ti.fib_batch(seed=0, count=2000)
+        t, cap, key = ti.FIB, 1 << 26, "fib-batch-10000"
+    elif wl == "ttree20":
+        f, o = ti.concat_terms([ti.ttree_term(20)])
+        t, cap, key = ti.TTREE, 1 << 23, "ttree"
+    else:
+        t, f, o, cap, _, _, key = build_workload(wl)
     prog = trs.trs_compile(t)
-    if not (kw or {}).get("generic"):
-        prog.specialise()   # the engine the bench times
+    prog.specialise()
     pool = trs.Pool(prog, cap)
-    kw = kw or autotune_defaults("frontier", wl)
+    kw = kw or autotune_defaults("frontier", key)
     for _ in range(reps):
         pool.trs_pool_reset()
-        pool.term_upload_batch(flat, offs)
-        if name in PRE_NORMALISE:
-            pool.trs_normalize(**PRE_NORMALISE[name])
-        try:
-            st = pool.trs_normalize(**kw)
-        except trs.TrsError as e:
-            if e.name != "TRS_ERR_SWEEP_LIMIT":
-                raise
-            st = {"status": e.name}
+        pool.term_upload_batch(f, o)
+        st = pool.trs_normalize(**kw)
         torch.cuda.synchronize()
     print(json.dumps({"case": name, "opts": kw, "stats": st}))
 
@@ -410,31 +601,33 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="frontier")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--headline-only", action="store_true", help="skip the per-workload blocks")
     args = ap.parse_args()
     if args.case:
         run_case(args.case, args.reps)
         return
     args.warmup = max(args.warmup, 3)
     rank, ws, local = dist_init()
+    threads = os.cpu_count() or 1
 
     if args.impl == "reference":
         if rank != 0:
             return
-        steps = []
+        _, _, _, _, _, desc, _ = build_workload(HEAD)
+        per = max(0.5, min(6.0, 120.0 / max(args.steps + args.warmup, 1)))
         for _ in range(args.warmup):
-            cpu_baseline(0.05)
-        base = None
+            oracle_sample(HEAD, 0.2, threads)
+        vals, base = [], None
         for _ in range(args.steps):
-            base = cpu_baseline(max(0.5, args.cpu_seconds / max(args.steps, 1)))
-            steps.append(base["value"])
-        v = statistics.mean(steps)
+            base = oracle_sample(HEAD, per, threads)
+            vals.append(base["value"])
+        v = statistics.mean(vals)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 186579 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": 726705404 / v * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "engine": "cpu oracle"},
+                "config": {"workload": desc, "engine": "cpu oracle (leftmost-innermost C rewriter)"},
                 "cpu_baseline": dict(base, value=v),
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -443,25 +636,25 @@ def main():
     r = run_ours(args, rank, ws, local)
     if rank != 0:
         return
-    cb = cpu_baseline(args.cpu_seconds)
+    cb = oracle_sample(HEAD, args.cpu_seconds, threads)
+    for name, blk in r["configs"].items():
+        if name != "ttree22":   # a single term of 117M rewrites: minutes on one core
+            blk["cpu_oracle"] = oracle_sample(name, 3.0 if name != "c5" else 0.1, threads)
     st = r["stats"]
+    o = r["opts"]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "engine": "specialised (rules compiled to CUDA at run time)",
-                   "mode": r["mode"], "driver": r["opts"].get("driver"),
-                   "block_size": r["opts"].get("block_size"), "solo_max": r["opts"].get("solo_max"),
-                   "eager": r["opts"].get("eager"),
-                   "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "time_to_nf_ms": r["ms"], "plain_sweep": r["plain"], "learned_frontier": r["learned"],
-        "table_driven_engine": r["table_driven"], "specialise_s": r["specialise_s"],
-        "speedup_vs_plain": r["plain"]["ms"] / r["ms"],
-        "learned_speedup_vs_plain": r["plain"]["ms"] / r["learned"]["ms"],
-        "sweeps": st["sweeps"], "rewrites": st["rewrites"],
-        "roofline": r["roofline"], "plain_scan": r["plain_scan"], "cpu_baseline": cb, "e2e": r["e2e"],
-        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+        "config": {"workload": r["desc"] if ws == 1 else f"{ws} x 4096 arithmetic trees, partitioned by cost",
+                   "engine": "specialised (rules compiled to CUDA at run time)", "mode": o.get("mode"),
+                   "driver": o.get("driver"), "block_size": o.get("block_size"),
+                   "solo_max": o.get("solo_max"), "eager": o.get("eager"),
+                   "l2": "inputs larger than L2 (5 GB of input records) and a 256 MiB write between steps",
+                   "parallelism": f"{ws} GPUs, terms sharded by cost" if ws > 1 else "1 GPU"},
+        "time_to_nf_ms": r["ms"], "rewrites": st["rewrites"], "sweeps": st["sweeps"],
+        "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"],
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "configs": r["configs"],
     }
     print(json.dumps(line))
 

@@ -206,10 +206,10 @@ typedef struct {
     int32_t refresh;         /* learned: sweeps between predictor refreshes */
     float threshold;         /* learned: predicted probability needed to enter the frontier */
     int32_t trace;           /* 1 = record one trs_sweep_record per sweep */
-    int32_t eager;           /* frontier mode: > 0 lets a thread go on with a node it
-                                just made ready, up to this many nodes per entry, in
-                                the same sweep (same results and counts, fewer
-                                sweeps); 0 = synchronous sweeps */
+    int32_t eager;           /* frontier and learned modes: > 0 lets a thread go on
+                                with a node it just made ready, up to this many
+                                nodes per entry, in the same sweep (same results and
+                                counts, fewer sweeps); 0 = synchronous sweeps */
     int64_t time_limit_ns;   /* wall-clock limit of the whole call (TRS_ERR_TIMEOUT) */
     int32_t generic;         /* 1 = run the table-driven engine even when the program
                                 has a specialised one (trs_specialise) */
@@ -275,7 +275,17 @@ typedef struct {
     int32_t visits;     /* nodes examined */
     int32_t allocs;     /* nodes created */
     int64_t high_water; /* high-water mark after the sweep */
+    int64_t t_ns;       /* device time from the start of the call to the end of
+                           this sweep (globaltimer) */
+    int32_t frontier;   /* frontier / learned: entries of the next frontier */
+    int32_t flags;      /* TRS_SWEEP_SOLO | TRS_SWEEP_GC | TRS_SWEEP_CONFIRM |
+                           TRS_SWEEP_REFRESH: how the sweep ran and what follows it */
 } trs_sweep_record;
+
+#define TRS_SWEEP_SOLO    1  /* run by one block (a solo episode) */
+#define TRS_SWEEP_GC      2  /* a garbage collection follows */
+#define TRS_SWEEP_CONFIRM 4  /* a full confirmation scan follows */
+#define TRS_SWEEP_REFRESH 8  /* learned: a predictor refresh follows */
 
 /* Copy the trace of the last trs_normalize (opts.trace = 1) to buf (host).
  * Records beyond the pool's trace capacity (65536) keep only the last ones.
@@ -378,14 +388,18 @@ int trs_pool_attach_predictor(trs_pool *pool, const trs_predictor *pred);
  *
  * d_term: device, the input term in preorder (len symbols); d_out: device,
  * out_cap entries, receives the normal form in preorder; d_out_len: device,
- * one int64, receives its length (-1 if it did not fit).  opts: NULL or plain /
- * frontier mode with the persistent driver.  stats: host, may be NULL.  The
- * call is synchronous: it waits for `stream` and returns the device status.
+ * one int64, receives its length (-1 if it did not fit, 0 if the term was
+ * rejected).  opts: NULL or plain / frontier mode with the persistent driver.
+ * stats: host, may be NULL.  The call is synchronous: it ends by copying the
+ * control block to host memory and waiting for `stream`, and returns the
+ * device status.  A malformed preorder in d_term returns TRS_ERR_BAD_TERM.
  *
  * Limits: the array is 24 MiB on every GPU that loads the library and stays
- * allocated until the process exits; it holds (24 MiB - rule tables) /
- * (4 * (9 + maxarity)) node slots (about 570,000 for a signature of maximum
- * arity 2).  A term of len >= that many slots is rejected with
+ * allocated until the process exits; it holds (24 MiB - control block - rule
+ * tables) / (4 * (rs + 6) + 1/8) node slots, where rs is the record stride in
+ * words (8 for a maximum arity up to 4, 16 above): about 448,000 slots up to
+ * arity 4 and about 285,000 above.  A term of len >= that many slots is
+ * rejected with
  * TRS_ERR_TOO_BIG before any GPU work; running out of slots while rewriting
  * returns TRS_ERR_POOL_FULL; a normal form longer than out_cap returns
  * TRS_ERR_BUFFER_SMALL.  The first call on a device looks up the array's device

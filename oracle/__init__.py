@@ -117,3 +117,24 @@ def normalize_many(trs, terms, mode: str = "innermost"):
     """Normalise a list of terms one by one (single thread)."""
     o = Oracle(trs)
     return [o.normalize(t, mode) for t in terms]
+
+
+def normalize_threads(trs, terms, threads: int | None = None, mode: str = "innermost"):
+    """Normalise independent terms on `threads` host threads (one Oracle per
+    thread; the C calls release the GIL).  Returns the results in order."""
+    import concurrent.futures as cf
+    threads = threads or os.cpu_count() or 1
+    terms = list(terms)
+    chunks = [terms[i::threads] for i in range(threads)]
+
+    def work(ch):
+        o = Oracle(trs)
+        return [o.normalize(t, mode) for t in ch]
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(work, chunks))
+    out = [None] * len(terms)
+    for r, part in enumerate(parts):
+        for j, res in enumerate(part):
+            out[r + j * threads] = res
+    return out

@@ -75,7 +75,8 @@ class Stats(ctypes.Structure):
 
 class SweepRecord(ctypes.Structure):
     _fields_ = [("sweep", _i64), ("rewrites", _i32), ("nf_marks", _i32), ("visits", _i32),
-                ("allocs", _i32), ("high_water", _i64)]
+                ("allocs", _i32), ("high_water", _i64), ("t_ns", _i64), ("frontier", _i32),
+                ("flags", _i32)]
 
 
 def _sig(name, res, *args):
@@ -331,8 +332,8 @@ class Pool:
         n = _i64()
         _check(lib.trs_trace_read(self._h, buf, cap, ctypes.byref(n), _stream(stream)),
                "trs_trace_read")
-        return [(r.sweep, r.rewrites, r.nf_marks, r.visits, r.allocs, r.high_water)
-                for r in buf[:n.value]]
+        return [(r.sweep, r.rewrites, r.nf_marks, r.visits, r.allocs, r.high_water, r.t_ns,
+                 r.frontier, r.flags) for r in buf[:n.value]]
 
 
 def _aligned_buffer(nbytes, device=None):
@@ -427,11 +428,43 @@ class Predictor:
         return out
 
 
+def _check_static_tensor(name, t, dtype, min_numel=0):
+    """Argument checks of trs_normalize_static: the C call takes raw device
+    pointers and would read or write through a wrong one (a host pointer, a
+    tensor of another device, another element type or a strided view)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"trs_normalize_static: {name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"trs_normalize_static: {name} must have dtype {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"trs_normalize_static: {name} must be contiguous")
+    if t.numel() < min_numel:
+        raise ValueError(f"trs_normalize_static: {name} needs at least {min_numel} element(s)")
+
+
+def _check_static_device(name, t):
+    import torch
+    if t.device.type != "cuda":
+        raise ValueError(f"trs_normalize_static: {name} must be a CUDA tensor, not on {t.device}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"trs_normalize_static: {name} is on {t.device}, but the current device "
+                         f"is cuda:{torch.cuda.current_device()}")
+
+
 def trs_normalize_static(program: Program, d_term, d_out, d_out_len, stream=None, **kw) -> dict:
     """Normalise one term with the library's fixed device array as the node
-    store (no allocation).  d_term: int32 CUDA tensor (preorder); d_out: int32
-    CUDA tensor receiving the normal form; d_out_len: int64 CUDA tensor of one
-    element receiving its length.  Returns the statistics."""
+    store (no allocation).  d_term: contiguous int32 CUDA tensor (preorder);
+    d_out: contiguous int32 CUDA tensor receiving the normal form; d_out_len:
+    int64 CUDA tensor of at least one element receiving its length.  All three
+    on the current device (TypeError / ValueError otherwise, before any GPU
+    work).  Returns the statistics."""
+    import torch
+    _check_static_tensor("d_term", d_term, torch.int32, 1)
+    _check_static_tensor("d_out", d_out, torch.int32)
+    _check_static_tensor("d_out_len", d_out_len, torch.int64, 1)
+    for name, t in (("d_term", d_term), ("d_out", d_out), ("d_out_len", d_out_len)):
+        _check_static_device(name, t)
     o = default_opts(**kw)
     st = Stats()
     _check(lib.trs_normalize_static(program._h, _vp(d_term.data_ptr()), d_term.numel(),

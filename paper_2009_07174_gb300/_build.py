@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtrs_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
-SOURCES = ["trs_compile.cpp", "trs_api.cu", "trs_kernels.cu", "trs_mlp.cu", "trs_static.cu", "trs_spec.cpp"]
+SOURCES = ["trs_compile.cpp", "trs_api.cu", "trs_kernels.cu", "trs_mlp.cu", "trs_static.cu", "trs_spec.cpp", "trs_transfer.cu"]
 # engine headers compiled into the library for the run-time specialised engine
 # (name as written in the #include directives -> file)
 JIT_HEADERS = [("trs_device.cuh", "csrc/trs_device.cuh"), ("trs_engine.h", "csrc/trs_engine.h"),

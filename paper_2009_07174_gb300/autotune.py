@@ -22,15 +22,15 @@ DEFAULTS = {
     "frontier": {"mode": "frontier", "driver": "persistent", "block_size": 512, "solo_max": 512,
                  "eager": 64},
     "learned": {"mode": "learned", "driver": "persistent", "block_size": 512, "solo_max": 512,
-                "refresh": 16, "threshold": 0.5},
+                "refresh": 16, "threshold": 0.5, "eager": 256},
 }
 
 SPACE = {
     "plain": {"block_size": [128, 256, 512], "driver": ["persistent", "graph"]},
     "frontier": {"block_size": [128, 256, 512], "solo_max": [0, 512], "eager": [0, 16, 64, 256, 1024],
                  "driver": ["persistent", "graph"]},
-    "learned": {"block_size": [256, 512], "solo_max": [0, 512], "refresh": [8, 16, 64],
-                "threshold": [0.2, 0.5, 0.8]},
+    "learned": {"block_size": [256, 512], "solo_max": [0, 512], "refresh": [16, 64],
+                "threshold": [0.2, 0.5, 0.8], "eager": [0, 64, 256, 1024]},
 }
 
 

@@ -25,6 +25,14 @@ void *graph_cond_ptr();
 const unsigned char *predictor_block(const trs_predictor *p);
 size_t predictor_block_bytes(const trs_predictor *p);
 const trs_program *predictor_program(const trs_predictor *p);
+// trs_transfer.cu
+size_t upload_aux_bytes(long long total, long long nterms);
+int device_upload(const DevPool &P, const int32_t *flat, const int64_t *offsets, long long nterms, long long base,
+                  int32_t stamp, int32_t *d_flat, int32_t *d_e, int32_t *d_par, void *aux, int num_sms,
+                  cudaStream_t s, cudaError_t *cuda_err);
+int device_download(const DevPool &P, long long n_top, const int32_t *roots, int nroots, int32_t *buf,
+                    int64_t cap, int64_t *offsets_out, void *scratch, size_t scratch_bytes, int num_sms,
+                    long long limit_ns, cudaStream_t s, cudaError_t *cuda_err);
 }  // namespace trs
 
 using namespace trs;
@@ -57,11 +65,14 @@ struct trs_pool {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kHostWalkBytes = 16u << 20;            // records walked on the host up to this size
+constexpr int64_t kDeviceUploadMin = 1 << 16;           // batches from this many symbols build on the device
+constexpr long long kWalkLimitNs = 30LL * 1000 * 1000 * 1000;  // device walks give up after this
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t rec, nfs, ring, fq0, fq1, act, trace, ctl, tab, total;
+    size_t rec, nfs, ring, fq0, fq1, act, cand, dbm, trace, ctl, tab, total;
 };
 
 Layout layout(const Program &p, int64_t cap)
@@ -76,6 +87,8 @@ Layout layout(const Program &p, int64_t cap)
     L.fq0 = take(slots);
     L.fq1 = take(slots);
     L.act = take(slots);
+    L.cand = take(slots);
+    L.dbm = take(((size_t)cap + 31) / 32 * sizeof(uint32_t));
     L.trace = take(sizeof(trs_sweep_record) * (size_t)kTraceCap);
     L.ctl = take(sizeof(Ctl));
     L.tab = take(p.table.size() * sizeof(int32_t));
@@ -177,6 +190,8 @@ int trs_pool_create(const trs_program *prog, int64_t capacity, void *dev_mem, si
     d.fq[1] = (int32_t *)(b + L.fq1);
     d.act = nullptr;
     pool->act = (int32_t *)(b + L.act);
+    d.cand = (int32_t *)(b + L.cand);
+    d.dbm = (uint32_t *)(b + L.dbm);
     d.trace = (trs_sweep_record *)(b + L.trace);
     d.ctl = (Ctl *)(b + L.ctl);
     d.tab = (const int32_t *)(b + L.tab);
@@ -223,14 +238,12 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
     }
     if (nterms == 0) return TRS_OK;
     const Program &p = pool->prog->p;
-    const int64_t total = offsets[nterms] - offsets[0];
-    for (int32_t t = 0; t < nterms; t++) {
-        if (offsets[t + 1] < offsets[t] ||
-            !valid_term(p, flat + offsets[t], offsets[t + 1] - offsets[t])) {
-            set_error("term_upload_batch: term " + std::to_string(t) + " is not a ground term");
+    for (int32_t t = 0; t < nterms; t++)
+        if (offsets[t + 1] <= offsets[t]) {
+            set_error("term_upload_batch: term " + std::to_string(t) + " is empty");
             return TRS_ERR_BAD_TERM;
         }
-    }
+    const int64_t total = offsets[nterms] - offsets[0];
     Ctl h;
     int st = read_ctl(pool, &h, stream);
     if (st != TRS_OK) return st;
@@ -238,6 +251,33 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
     if (base + total > pool->d.cap) {
         set_error("term_upload_batch: pool full");
         return TRS_ERR_POOL_FULL;
+    }
+    const DevPool &d = pool->d;
+    // Large batches are built on the device (trs_transfer.cu): only the
+    // preorder symbols and offsets cross, the frontier buffers and the
+    // predictor-trace array hold the per-symbol scratch, and the records of
+    // the slots being filled hold the rest until they are written.
+    const size_t rec_area = (size_t)total * d.rs * sizeof(int32_t);
+    if (total >= kDeviceUploadMin && upload_aux_bytes(total, nterms) <= rec_area) {
+        cudaError_t ce = cudaSuccess;
+        st = device_upload(d, flat, offsets, nterms, base, -(int32_t)h.sweep_id, d.fq[0], d.fq[1], pool->act,
+                           (void *)(d.rec + (size_t)base * d.rs), pool->num_sms, stream, &ce);
+        if (st == TRS_ERR_CUDA) return cuda_fail(ce, "term_upload_batch (device build)");
+        if (st == TRS_ERR_BAD_TERM) {
+            set_error("term_upload_batch: the batch is not a sequence of well-formed ground terms");
+            return st;
+        }
+        for (int32_t t = 0; t < nterms; t++) roots_out[t] = (int32_t)(base + offsets[t] - offsets[0]);
+        long long ntop = base + total;
+        CK(cudaMemcpyAsync(&d.ctl->n_top, &ntop, sizeof(ntop), cudaMemcpyHostToDevice, stream), "upload n_top");
+        CK(cudaStreamSynchronize(stream), "upload synchronize");
+        return TRS_OK;
+    }
+    for (int32_t t = 0; t < nterms; t++) {
+        if (!valid_term(p, flat + offsets[t], offsets[t + 1] - offsets[t])) {
+            set_error("term_upload_batch: term " + std::to_string(t) + " is not a ground term");
+            return TRS_ERR_BAD_TERM;
+        }
     }
     const int ma = p.maxarity, rs = rec_stride(ma);
     // records: head, arguments, parent word, count 1 (the tree edge or the
@@ -267,7 +307,6 @@ int term_upload_batch(trs_pool *pool, const int32_t *flat, const int64_t *offset
         roots_out[t] = (int32_t)(base + b);
     }
     const size_t sz = (size_t)total * sizeof(int32_t);
-    const DevPool &d = pool->d;
     CK(cudaMemcpyAsync(d.rec + (size_t)base * rs, rec.data(), sz * rs, cudaMemcpyHostToDevice, stream),
        "upload records");
     CK(cudaMemcpyAsync(d.nfs + base, nfs.data(), sz, cudaMemcpyHostToDevice, stream), "upload nfs");
@@ -400,7 +439,7 @@ int trs_normalize(trs_pool *pool, const trs_opts *opts, trs_stats *stats, trs_st
     lo.threshold = o.threshold;
     lo.timeout_ns = o.timeout_ns;
     lo.time_limit_ns = o.time_limit_ns;
-    lo.eager = o.mode == TRS_MODE_FRONTIER ? o.eager : 0;
+    lo.eager = o.mode != TRS_MODE_PLAIN ? o.eager : 0;
     pool->last = lo;
     pool->last_driver = o.driver;
     pool->last_spec = fn != nullptr;
@@ -514,7 +553,7 @@ int trs_pool_stats(trs_pool *pool, trs_stats *s, trs_stream stream)
     s->refreshes = h.st_refreshes;
     s->frontier_peak = h.st_frontier_peak;
     s->high_water = h.n_top;
-    // dead nodes are counted from above between collections: a lower bound
+    // slots in use, less the free ring and the dead nodes not yet collected
     s->live_nodes = (h.n_top - 1) - (h.fl_end - h.fl_begin) - h.dead;
     s->solo_sweeps = h.st_solo_sweeps;
     s->specialised = pool->last_spec;
@@ -532,26 +571,47 @@ int term_download_batch(trs_pool *pool, const int32_t *roots, int32_t nroots, in
         set_error("term_download: bad argument");
         return TRS_ERR_ARG;
     }
+    if (nroots == 0) {
+        if (offsets_out) offsets_out[0] = 0;
+        return TRS_OK;
+    }
     const Program &p = pool->prog->p;
     Ctl h;
     int st = read_ctl(pool, &h, stream);
     if (st != TRS_OK) return st;
     const int64_t n = h.n_top;
     const DevPool &d = pool->d;
-    for (int32_t r = 0; r < nroots; r++) {
+    for (int32_t r = 0; r < nroots; r++)
         if (roots[r] <= 0 || roots[r] >= n) { set_error("term_download: root out of range"); return TRS_ERR_STATE; }
-        int32_t v[2];
-        CK(cudaMemcpyAsync(&v[0], d.nfs + roots[r], sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "read root");
-        CK(cudaMemcpyAsync(&v[1], d.rec + (size_t)roots[r] * d.rs + rec_rc(p.maxarity), sizeof(int32_t),
-                           cudaMemcpyDeviceToHost, stream), "read root");
-        CK(cudaStreamSynchronize(stream), "read root");
-        if (v[0] == 0 || v[1] <= 0) { set_error("term_download: root is not live"); return TRS_ERR_STATE; }
-    }
     const int rs = d.rs;
+    // A store whose records below the high-water mark fit kHostWalkBytes is
+    // copied back in one piece and walked on the host: for it that is cheaper
+    // than the device pass.  Larger stores are serialised on the device
+    // (trs_transfer.cu) in the frontier buffers and the predictor-trace array,
+    // which hold nothing between normalisations; only the result crosses.
+    if ((size_t)n * rs * sizeof(int32_t) > kHostWalkBytes) {
+        char *scratch = (char *)d.fq[0];
+        const size_t scratch_bytes = (size_t)((char *)d.cand - scratch);
+        cudaError_t ce = cudaSuccess;
+        st = device_download(d, n, roots, nroots, buf, cap, offsets_out, scratch, scratch_bytes, pool->num_sms,
+                             kWalkLimitNs, stream, &ce);
+        if (st == TRS_ERR_CUDA) return cuda_fail(ce, "term_download (device pass)");
+        if (st == TRS_OK) return TRS_OK;
+        if (st == TRS_ERR_BUFFER_SMALL) { set_error("term_download: buffer too small"); return st; }
+        if (st == TRS_ERR_STATE) { set_error("term_download: a root is not live, or the store is corrupt"); return st; }
+        if (st == TRS_ERR_TIMEOUT) { set_error("term_download: a walk ran out of time (corrupt store)"); return st; }
+        // TRS_ERR_TOO_BIG: a subtree deeper than the device stacks; walk on the host
+    }
     std::vector<int32_t> rec((size_t)n * rs);
     CK(cudaMemcpyAsync(rec.data(), d.rec, (size_t)n * rs * sizeof(int32_t), cudaMemcpyDeviceToHost, stream),
        "download records");
     CK(cudaStreamSynchronize(stream), "download synchronize");
+    // a root is live while it is referenced (freed slots have count 0)
+    for (int32_t r = 0; r < nroots; r++)
+        if (rec[(size_t)roots[r] * rs + rec_rc(p.maxarity)] <= 0) {
+            set_error("term_download: root is not live");
+            return TRS_ERR_STATE;
+        }
     int64_t out = 0;
     std::vector<int32_t> stk;
     offsets_out[0] = 0;
@@ -562,12 +622,12 @@ int term_download_batch(trs_pool *pool, const int32_t *roots, int32_t nroots, in
             int32_t x = stk.back();
             stk.pop_back();
             if (x <= 0 || x >= n) { set_error("term_download: dangling index"); return TRS_ERR_STATE; }
-            const int32_t *r = &rec[(size_t)x * rs];
-            int32_t s = r[kRecHead];
+            const int32_t *rr = &rec[(size_t)x * rs];
+            int32_t s = rr[kRecHead];
             if (s <= 0 || s >= p.nsym) { set_error("term_download: corrupt node"); return TRS_ERR_STATE; }
             if (out < cap) buf[out] = s;
             out++;
-            for (int a = p.arity[s] - 1; a >= 0; a--) stk.push_back(r[rec_arg(a)]);
+            for (int a = p.arity[s] - 1; a >= 0; a--) stk.push_back(rr[rec_arg(a)]);
         }
         offsets_out[r + 1] = out;
     }

@@ -41,6 +41,16 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p)
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ int ld_acquire_s32(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_s32(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -108,6 +118,10 @@ __device__ __forceinline__ void red_add_s32(int32_t *p, int32_t v)
 {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v));
 }
+__device__ __forceinline__ void red_or_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v));
+}
 
 // ---------------------------------------------------------------------------
 // staged rule table
@@ -138,21 +152,60 @@ struct State {
     long long n;     // high-water mark at the start of the sweep
     long long fb;    // free ring begin (at sweep start)
     long long fe;    // free ring end
-    long long dead;  // nodes with count 0 not yet reclaimed
+    long long dead;  // reference decrements since the last collection
     long long fsz;   // frontier size
     long long left;  // sweeps left in this call
     long long since; // learned: sweeps since the last refresh
     int cur;         // current frontier buffer
 };
 
+// Free-ring positions are kept below 2 * cap by the loop (begin < cap, the ring
+// holding at most cap entries), so a ring index is a position less a few
+// multiples of cap: no 64-bit division on the allocation path.
+__device__ __forceinline__ long long ring_wrap(long long x, long long cap)
+{
+    while (x >= cap) x -= cap;
+    return x;
+}
+
 struct Counters {    // per-thread, reduced per block at the end of a phase
     unsigned long long rewrites, nf_marks, visits, allocs, deaths;
 };
+
+// A reference count was decremented: mark the slot as a collection
+// candidate (one bit, fire and forget) and count a possible death for the
+// collection trigger.
+__device__ __forceinline__ void mark_candidate(const DevPool &P, int32_t x, Counters &C)
+{
+    red_or_u32(P.dbm + (x >> 5), 1u << (x & 31));
+    C.deaths++;
+}
+
+
 
 enum { M_PLAIN = 0, M_FRONTIER = 1, M_LEARNED = 2 };
 enum { D_SKIP = -1, D_MARK = -2, D_NONE = -3 };
 
 __device__ __forceinline__ bool is_nf_at(int32_t s, long long k) { return s > 0 && s <= k; }
+
+// Readiness of an argument c: R_SWEEP, in normal form as of the start of sweep
+// k (the synchronous sweep); R_NOW, in normal form now (an eager learned
+// continuation: any positive stamp, read with acquire so that the marker's
+// earlier writes are visible).
+enum { R_NONE = 0, R_SWEEP = 1, R_NOW = 2 };
+__device__ __forceinline__ bool nf_ready(const DevPool &P, int32_t c, long long k, int ready)
+{
+    return ready == R_NOW ? ld_acquire_s32(&P.nfs[c]) > 0 : is_nf_at(P.nfs[c], k);
+}
+
+// A node found to be in normal form in sweep k: plain store, or (learned
+// mode) a release store that orders the node's record before the stamp for
+// eager continuations that read it with nf_ready(R_NOW).
+__device__ __forceinline__ void store_nf(const DevPool &P, int mode, int32_t i, long long k)
+{
+    if (mode == M_LEARNED) st_release_s32(&P.nfs[i], (int32_t)(k + 1));
+    else P.nfs[i] = (int32_t)(k + 1);
+}
 
 // Content of a node this lane has just written (head and first arguments),
 // handed to the next step of an eager chain so that it need not be read back.
@@ -161,6 +214,13 @@ struct Carry {
     int32_t h;                  // 0: nothing carried
     int32_t c[kCarryArgs];
 };
+
+// Prefetch a node record into L1 (a hint: no register, no wait).  Used for
+// the records the next step of an eager chain will load.
+__device__ __forceinline__ void prefetch_rec(const DevPool &P, int32_t x)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(node_at(P, x)));
+}
 
 // Element j of a small per-thread array, by selects (the array stays in
 // registers).
@@ -196,7 +256,7 @@ constexpr int kPf = 2;  // arguments whose subterms are prefetched
 // second-level nodes in one more step, so that a pattern of depth two costs
 // two dependent loads instead of one per pattern node and rule.
 __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i, long long k,
-                                      bool check_ready, int32_t *reg, int32_t &h_out,
+                                      int check_ready, int32_t *reg, int32_t &h_out,
                                       const Carry &cin)
 {
     const long long cap = P.cap;
@@ -230,7 +290,7 @@ __device__ __forceinline__ int decide(const DevPool &P, const Tab &T, int32_t i,
         bool ready = true;
 #pragma unroll
         for (int j = 0; j < TRS_MAX_ARITY; j++)
-            if (j < ar && !is_nf_at(P.nfs[c[j]], k)) ready = false;
+            if (j < ar && !nf_ready(P, c[j], k, check_ready)) ready = false;
         if (!ready) return D_SKIP;
         if (r0 == r1) return D_MARK;
     }
@@ -333,7 +393,7 @@ __device__ __forceinline__ int32_t alloc_slot(const DevPool &P, const State &S, 
                                               bool &ok)
 {
     const long long avail = S.fe - S.fb;
-    if ((long long)pos < avail) return P.ring[(S.fb + (long long)pos) % P.cap];
+    if ((long long)pos < avail) return P.ring[ring_wrap(S.fb + (long long)pos, P.cap)];
     const long long s = S.n + ((long long)pos - avail);
     if (s >= P.cap) { ok = false; return 0; }
     return (int32_t)s;
@@ -346,7 +406,7 @@ __device__ __forceinline__ int32_t ring_ahead(const DevPool &P, const State &S, 
 {
     const long long avail = S.fe - S.fb;
     if (pos >= end || (long long)pos >= avail) return -1;
-    return P.ring[(S.fb + (long long)pos) % P.cap];
+    return P.ring[ring_wrap(S.fb + (long long)pos, P.cap)];
 }
 
 // m new slots for each lane (all 32 lanes call).  Lane l keeps the ring entry
@@ -421,12 +481,12 @@ __device__ __forceinline__ void warp_alloc_return(const DevPool &P, const State 
         const unsigned long long pos = W.pos + (unsigned long long)q;
         int32_t slot;
         if ((long long)pos < avail) {
-            slot = P.ring[(S.fb + (long long)pos) % P.cap];
+            slot = P.ring[ring_wrap(S.fb + (long long)pos, P.cap)];
         } else {
             slot = (int32_t)(S.n + ((long long)pos - avail));
             P.nfs[slot] = 0;            // never used: a free slot below the new mark
         }
-        P.ring[(S.fe + (long long)rb + q) % P.cap] = slot;
+        P.ring[ring_wrap(S.fe + (long long)rb + q, P.cap)] = slot;
     }
     W.pos = W.end;
 }
@@ -464,7 +524,10 @@ __device__ __forceinline__ void notify_parent(const DevPool &P, int32_t pv, int3
 {
     const int32_t p = pv & 0x7fffffff;
     if (p == 0) return;
-    if (pv < 0 || atom_acqrel_add_s32(&pend_at(P, p), -1) == 1) push[npush++] = p;
+    if (pv < 0 || atom_acqrel_add_s32(&pend_at(P, p), -1) == 1) {
+        push[npush++] = p;
+        prefetch_rec(P, p);   // the record the parent's step loads first
+    }
 }
 
 // Learned frontier: every node enters the next frontier at most once per
@@ -473,6 +536,17 @@ __device__ __forceinline__ void learned_push(const DevPool &P, int32_t x, long l
                                              int &npush)
 {
     if (atomicExch(&pend_at(P, x), (int32_t)k_next) != (int32_t)k_next) push[npush++] = x;
+}
+
+// Prefetch the records of the first kPf arguments of a continuation of head
+// sym that decide() will load (the table's prefetch plan).
+__device__ __forceinline__ void prefetch_args(const DevPool &P, const Tab &T, int32_t sym, const Carry &c, int na)
+{
+    const int plan = T.w[T.off_ar + sym] >> 8;
+#pragma unroll
+    for (int a = 0; a < kPf; a++)
+        if (a < na && a < kCarryArgs && (((plan >> (16 + a)) | (plan >> a) | (plan >> (4 + a))) & 1))
+            prefetch_rec(P, c.c[a]);
 }
 
 __device__ __forceinline__ int32_t par_word(const Tab &T, int32_t parent, int32_t parent_sym)
@@ -492,7 +566,7 @@ __device__ __forceinline__ int32_t build_sym(const int32_t *build, int root_narg
 __device__ __forceinline__ void apply_mark(const DevPool &P, int mode, int32_t i, int32_t pv, long long k,
                                            Counters &C, int32_t *push, int &npush)
 {
-    P.nfs[i] = (int32_t)(k + 1);  // in normal form from the next sweep on
+    store_nf(P, mode, i, k);  // in normal form from the next sweep on
     C.nf_marks++;
     if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
     if (mode == M_LEARNED) {
@@ -528,6 +602,11 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
     const int root_nargs = R[5] & 0xff;
     const int root_pend = (R[5] >> 8) & 0xff;
     const int32_t stamp_new = -(int32_t)(k + 1);  // not in normal form, eligible next sweep
+    // learned mode queues the nodes a rewrite makes ready for the next sweep,
+    // and the one queued last is the eager continuation.  A redex that waits
+    // for new arguments is not queued: each of them, on becoming a normal
+    // form, queues its parent (one claim per sweep), so the last one can take
+    // the redex as its own continuation in the same sweep.
 
     // new nodes
     int pos = root_nargs;
@@ -553,11 +632,16 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
             pend_at(P, x) = (int32_t)(k + 1);
             push[npush++] = x;
             last.h = 0;
+            if (pj == 0) {
+                last = cx;
+                prefetch_args(P, T, sym, cx, na);
+            }
         } else {
             pend_at(P, x) = pj;
             if (mode == M_FRONTIER && pj == 0) {
                 push[npush++] = x;
                 last = cx;
+                prefetch_args(P, T, sym, cx, na);
             }
         }
     }
@@ -577,19 +661,19 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         }
     }
     // net reference changes of matched nodes, positive ones first; fire and
-    // forget (no return value on the critical path): every decrement counts as
-    // a possible death for the collection trigger, collection finds the real
-    // ones
+    // forget (no return value on the critical path): a decremented node is
+    // marked as a collection candidate, and the collection frees those whose
+    // count is then 0
     for (int d = 0; d < ndelta; d++) {
         int32_t w = delta[d];
         int32_t q = w & 0xff, dv = w >> 8;
         red_add_s32(&rc_at(P, reg[q]), dv);
-        if (dv < 0) C.deaths++;
+        if (dv < 0) mark_candidate(P, reg[q], C);
     }
     if (rootvar) {
         hs_at(P, i) = xh;
         for (int a = 0; a < xa; a++) arg_at(P, a, i) = xc[a];
-        P.nfs[i] = (int32_t)(k + 1);
+        store_nf(P, mode, i, k);
         const int before = npush;
         if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);
         if (mode == M_LEARNED) {
@@ -608,13 +692,21 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
             if (a < kCarryArgs) ci.c[a] = v;
         }
         if (mode == M_LEARNED) {
-            learned_push(P, i, k + 1, push, npush);
-            last.h = 0;
+            if (root_pend == 0) {
+                const int before = npush;
+                learned_push(P, i, k + 1, push, npush);
+                last.h = 0;
+                if (npush != before) {
+                    last = ci;
+                    prefetch_args(P, T, R[1], ci, root_nargs);
+                }
+            }
         } else {
             pend_at(P, i) = root_pend;
             if (mode == M_FRONTIER && root_pend == 0) {
                 push[npush++] = i;
                 last = ci;
+                prefetch_args(P, T, R[1], ci, root_nargs);
             }
         }
     }
@@ -654,7 +746,7 @@ __device__ __forceinline__ void flush_counters(Counters &C, Acc *A)
 // contract as decide() and apply(), with the rules as straight-line code
 // (defined by the run-time compiled source after this header).
 __device__ __forceinline__ int spec_decide(const DevPool &P, const Tab &T, int32_t i, long long k,
-                                           bool check_ready, int32_t *reg, int32_t &h_out,
+                                           int check_ready, int32_t *reg, int32_t &h_out,
                                            const Carry &cin);
 __device__ __forceinline__ void spec_apply(const DevPool &P, const Tab &T, int mode, int32_t i, int32_t h,
                                            int32_t pv, int r, long long k, const int32_t *reg,
@@ -671,7 +763,7 @@ constexpr int kInPlace = 64;  // steps of one constant chain
 // (lane-uniform control flow; `cand` marks lanes with a node to consider).
 __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, const State &S,
                                                 Acc *A, WarpAlloc &W, int mode, bool cand, bool keep,
-                                                int32_t i, bool check_ready, int32_t *next_buf,
+                                                int32_t i, int check_ready, int32_t *next_buf,
                                                 Counters &C, bool eager, Carry &carry, bool climb = false)
 {
     int32_t reg[TRS_MAX_PATTERN];
@@ -691,7 +783,12 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
 #else
         d = decide(P, T, i, S.k, check_ready, reg, h, carry);
 #endif
-        if (mode == M_LEARNED && d == D_SKIP) learned_push(P, i, S.k + 1, push, npush);  // still waiting
+        if (mode == M_LEARNED && d == D_SKIP) {
+            // still waiting: a continuation is this lane's (claimed for the
+            // next sweep already), an entry joins the next sweep once
+            if (check_ready == R_NOW) push[npush++] = i;
+            else learned_push(P, i, S.k + 1, push, npush);
+        }
     }
 #ifdef TRS_JIT
     int m = (d >= 0) ? spec_new_count(d) : 0;
@@ -704,7 +801,8 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     Carry last;
     last.h = 0;
 #ifdef TRS_JIT
-    if (d >= 0 || d == D_MARK) spec_apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush, last);
+    if (d >= 0 || d == D_MARK)
+        spec_apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush, last);
 #else
     if (d >= 0 || d == D_MARK) apply(P, T, mode, i, h, pv, d, S.k, reg, nw, C, push, npush, last);
 #endif
@@ -714,7 +812,7 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     // that node in this step, its content travels with it
     int32_t cont = -1;
     carry.h = 0;
-    if (eager && npush > 0) {
+    if (eager && npush > 0 && (d >= 0 || d == D_MARK)) {
         cont = push[--npush];
         carry = last;
     }
@@ -729,10 +827,10 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
         for (int n = 0; n < kInPlace; n++) {
             int32_t h2 = 0;
 #ifdef TRS_JIT
-            const int d2 = spec_decide(P, T, i, S.k, false, reg, h2, carry);
+            const int d2 = spec_decide(P, T, i, S.k, R_NONE, reg, h2, carry);
             if (d2 < 0 || spec_new_count(d2) > 0) break;
 #else
-            const int d2 = decide(P, T, i, S.k, false, reg, h2, carry);
+            const int d2 = decide(P, T, i, S.k, R_NONE, reg, h2, carry);
             if (d2 < 0 || ((T.rule(d2)[0] >> 8) & 0xff) > 0) break;
 #endif
             Carry last2;
@@ -851,7 +949,7 @@ __device__ __forceinline__ void plain_chunks(const DevPool &P, const Tab &T, con
             const long long slot = ch * kWarpSlots + (long long)(b >> 2) * 128 + lane * 4 + (b & 3);
             Carry none;
             none.h = 0;
-            process_warp(P, T, S, A, W, M_PLAIN, cand, false, (int32_t)slot, true, nullptr, C, false, none);
+            process_warp(P, T, S, A, W, M_PLAIN, cand, false, (int32_t)slot, R_SWEEP, nullptr, C, false, none);
         }
     }
 }
@@ -878,15 +976,20 @@ __device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, cons
 // entries (one atomic per warp), so chains of dependent rewrites advance many
 // steps per sweep.  Results and counts are those of the synchronous sweep;
 // only the number of sweeps changes.
+// `narrow` (a grid sweep whose frontier has no more entries than the grid has
+// warps): a warp takes one entry at a time, and only when all its lanes are
+// idle, so each chain runs on a warp of its own and the constructor climb
+// (`climb`) holds no other lane back.
 __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
-                               long long warp0, long long nwarps, int eager = 0, bool climb = false)
+                               long long warp0, long long nwarps, int eager = 0, bool climb = false,
+                               bool narrow = false)
 {
     Counters C{0, 0, 0, 0, 0};
     WarpAlloc W = warp_alloc_begin(P, S);
     const int lane = threadIdx.x & 31;
     const int32_t *cur = P.fq[S.cur];
     int32_t *next = P.fq[S.cur ^ 1];
-    if (eager <= 0 || mode != M_FRONTIER) {
+    if (eager <= 0 || mode == M_PLAIN) {
         const long long nchunks = (S.fsz + 31) / 32;
         for (long long ch = warp0; ch < nchunks; ch += nwarps) {
             long long e = ch * 32 + lane;
@@ -905,10 +1008,17 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
             if (!__any_sync(kFull, cand || keep)) continue;
             Carry none;
             none.h = 0;
-            process_warp(P, T, S, A, W, mode, cand, keep, i, mode == M_LEARNED, next, C, false, none);
+            process_warp(P, T, S, A, W, mode, cand, keep, i, mode == M_LEARNED ? R_SWEEP : R_NONE, next, C,
+                         false, none);
         }
     } else {
+        // learned mode: an entry taken from the frontier is checked against
+        // the start of the sweep, like the synchronous sweep (an entry can
+        // only be ready if no lane of this sweep made it so, so no two lanes
+        // process one node); a continuation this lane claimed is checked
+        // against the current state
         int32_t node = -1;
+        bool node_fresh = false;
         int steps = 0;
         bool drained = false;
         Carry carry;
@@ -929,35 +1039,48 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
                 if (lane == 0) fl_seen = *(volatile unsigned long long *)&A->fl_claims;
             }
             const bool idle = node < 0;
-            const unsigned im = __ballot_sync(kFull, idle);
+            const unsigned im0 = __ballot_sync(kFull, idle);
+            const unsigned im = narrow ? (im0 == kFull ? 1u : 0u) : im0;
             bool fresh_entry = false;
+            int32_t kept = -1;   // learned: an entry not yet eligible, queued again
             if (im && !drained) {
                 const int leader = __ffs(im) - 1;
                 unsigned long long base = 0;
                 if (lane == leader) base = atomicAdd(&A->taken, (unsigned long long)__popc(im));
                 base = __shfl_sync(kFull, base, leader);
                 if ((long long)base >= S.fsz) drained = true;
-                if (idle) {
+                if ((im >> lane) & 1) {
                     long long e = (long long)base + __popc(im & ((1u << lane) - 1u));
                     if (e < S.fsz) {
                         int32_t i = cur[e];
                         int32_t s = P.nfs[i];
-                        if (s < 0 && -(long long)s <= S.k) { node = i; fresh_entry = true; carry.h = 0; }
+                        if (s < 0 && -(long long)s <= S.k) {
+                            node = i;
+                            fresh_entry = true;
+                            carry.h = 0;
+                        } else if (s < 0 && mode == M_LEARNED) {
+                            kept = i;
+                        }
                     }
                 }
             }
-            if (fresh_entry) steps = 0;
+            if (fresh_entry) {
+                steps = 0;
+                node_fresh = true;
+            }
             const bool cand = node >= 0;
-            if (!__any_sync(kFull, cand)) {
+            if (!__any_sync(kFull, cand || kept >= 0)) {
                 if (drained) break;
                 continue;
             }
-            int32_t cont = process_warp(P, T, S, A, W, mode, cand, false, cand ? node : 0, false, next, C,
-                                        true, carry, climb);
+            const int ready = mode == M_LEARNED ? (node_fresh ? R_SWEEP : R_NOW) : R_NONE;
+            int32_t cont = process_warp(P, T, S, A, W, mode, cand, kept >= 0, cand ? node : (kept >= 0 ? kept : 0),
+                                        ready, next, C, true, carry, climb);
             steps++;
             const bool over = cont >= 0 && (steps >= eager || pressure);
             if (__any_sync(kFull, over)) warp_push(next, &A->pushes, P.cap, over ? 1 : 0, &cont, P.ctl);
             node = over ? -1 : cont;
+            node_fresh = false;
         }
     }
     warp_alloc_return(P, S, A, W);
@@ -1005,82 +1128,127 @@ __device__ __forceinline__ int block_scan_flag(bool f, int *total)
     return block_scan_count(f ? 1 : 0, total);
 }
 
-// Garbage collection (Sec. 3, collect_free_indices): every slot whose reference
-// count is 0 and that is not already free releases its arguments and joins
-// the free ring.  A slot is claimed by swapping its stamp to 0, so the thread
-// that scans it and a thread that just dropped its count to 0 cannot both free
-// it; the latter follows the chain of nodes it kills (up to kGcWalk per slot),
-// so dropped subterms are reclaimed in one pass.  Appends to the ring are
-// compacted with a block scan, one atomic per block and chunk.
+// Garbage collection (Sec. 3, collect_free_indices).  The paper scans every
+// slot for a count of 0.  Here every decrement has set its slot's bit in the
+// candidate bitmap, so a collection reads cap / 8 bytes of bitmap instead of
+// the store, and visits only the decremented slots:
+//   phase_gc_collect: the set bits are cleared and compacted into the
+//     candidate list (one atomic per warp and 32 bitmap words);
+//   phase_gc_free: each candidate whose count is 0 is claimed by swapping its
+//     stamp to 0 (so a slot is freed once even when two threads reach it),
+//     releases its arguments and follows the nodes this kills, up to kGcWalk
+//     nodes per candidate; dead nodes beyond that get their bit set again and
+//     are freed by the next collection.  Freed slots join the free ring with
+//     one atomic per warp.
+// Warps run independently (no block barrier inside the loops), so a long
+// cascade holds back only its own warp.
 constexpr int kGcWalk = 24;
-constexpr int kGcPer = 4;  // slots per thread per chunk (one int4 of stamps)
 
-__device__ __forceinline__ void phase_gc(const DevPool &P, const Tab &T, const State &S, Acc *A,
-                                         long long block0, long long nblocks)
+__device__ __forceinline__ void phase_gc_collect(const DevPool &P, const State &S, Acc *A,
+                                                 long long warp0, long long nwarps)
 {
-    __shared__ unsigned long long s_base;
-    unsigned long long frees = 0, left = 0;
-    const long long n = S.n;
-    const long long per = (long long)blockDim.x * kGcPer;
-    const long long nchunks = (n + per - 1) / per;
-    for (long long ch = block0; ch < nchunks; ch += nblocks) {
-        const long long base = ch * per + (long long)threadIdx.x * kGcPer;
-        int32_t sv[kGcPer] = {0, 0, 0, 0};
-        if (base + kGcPer <= n) {
-            const int4 s4 = *reinterpret_cast<const int4 *>(P.nfs + base);
-            sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
-        } else {
-            for (int t = 0; t < kGcPer; t++)
-                if (base + t < n) sv[t] = P.nfs[base + t];
+    const int lane = threadIdx.x & 31;
+    const long long nwords = (S.n + 31) / 32;
+    for (long long g = warp0 * 32; g < nwords; g += nwarps * 32) {
+        const long long w = g + lane;
+        uint32_t v = 0;
+        if (w < nwords) {
+            v = P.dbm[w];
+            if (v) P.dbm[w] = 0;
         }
+        const int cnt = __popc(v);
+        int x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const int total = __shfl_sync(kFull, x, 31);
+        if (total == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(&A->gc_cand, (unsigned long long)total);
+        base = __shfl_sync(kFull, base, 31);
+        long long at = (long long)base + (x - cnt);
+        while (v) {
+            const int bit = __ffs(v) - 1;
+            v &= v - 1;
+            if (at < P.cap) P.cand[at] = (int32_t)(w * 32 + bit);
+            at++;
+        }
+    }
+}
+
+__device__ __forceinline__ void phase_gc_free(const DevPool &P, const Tab &T, const State &S, Acc *A,
+                                              long long ncand, long long warp0, long long nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long frees = 0, left = 0;
+    if (ncand > P.cap) ncand = P.cap;
+    for (long long g = warp0 * 32; g < ncand; g += nwarps * 32) {
+        const long long e = g + lane;
         int32_t freed[kGcWalk];
         int nfreed = 0;
-        for (int t = 0; t < kGcPer; t++) {
-            const long long i = base + t;
-            if (i < 1 || sv[t] == 0 || rc_at(P, i) != 0) continue;
-            if (atomicExch(&P.nfs[i], 0) == 0) continue;
-            // claimed: free it and follow the nodes it kills, keeping room for
-            // this thread's remaining slots
+        const int32_t x0 = e < ncand ? P.cand[e] : 0;
+        // head, arguments and count of the candidate in one go (one sector)
+        int4 q0 = make_int4(0, 0, 0, 0);
+        int32_t rc0 = 1;
+        if (x0 > 0) {
+            q0 = rec_head4(P, x0);
+            rc0 = rc_at(P, x0);
+        }
+        if (x0 > 0 && rc0 == 0 && atomicExch(&P.nfs[x0], 0) != 0) {
             int32_t stk[kGcWalk];
             int sp = 0;
-            stk[sp++] = (int32_t)i;
-            const int room = kGcWalk - (kGcPer - 1 - t);
+            stk[sp++] = x0;
             while (sp > 0) {
                 const int32_t x = stk[--sp];
                 freed[nfreed++] = x;
-                const int ar = T.arity(hs_at(P, x));
+                const int4 q = x == x0 ? q0 : rec_head4(P, x);
+                const int ar = T.arity(q.x);
+                // the first two decrements are in flight together
+                int od[2];
+#pragma unroll
+                for (int a = 0; a < 2; a++) od[a] = a < ar ? atomicSub(&rc_at(P, quad_word(q, 1 + a)), 1) : 0;
                 for (int a = 0; a < ar; a++) {
-                    const int32_t c = arg_at(P, a, x);
-                    if (atomicSub(&rc_at(P, c), 1) == 1) {
-                        if (nfreed + sp < room) {
-                            if (atomicExch(&P.nfs[c], 0) != 0) stk[sp++] = c;
-                        } else {
-                            left++;  // dead, reclaimed by a later pass
-                        }
+                    const int32_t c = a < 3 ? quad_word(q, 1 + a) : arg_at(P, a, x);
+                    const int old = a < 2 ? (a == 0 ? od[0] : od[1]) : atomicSub(&rc_at(P, c), 1);
+                    if (old != 1) continue;
+                    if (nfreed + sp < kGcWalk) {
+                        if (atomicExch(&P.nfs[c], 0) != 0) stk[sp++] = c;
+                    } else {
+                        red_or_u32(P.dbm + (c >> 5), 1u << (c & 31));  // freed by the next collection
+                        left++;
                     }
                 }
             }
         }
         frees += nfreed;
-        int total = 0;
-        const int off = block_scan_count(nfreed, &total);
-        if (total > 0) {
-            if (threadIdx.x == 0) s_base = atomicAdd(&A->gc_append, (unsigned long long)total);
-            __syncthreads();
-            for (int j = 0; j < nfreed; j++)
-                P.ring[(S.fe + (long long)s_base + off + j) % P.cap] = freed[j];
-            __syncthreads();
+        // warp-aggregated append of the freed slots to the ring
+        int x = nfreed;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const int total = __shfl_sync(kFull, x, 31);
+        if (total == 0) continue;
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(&A->gc_append, (unsigned long long)total);
+        base = __shfl_sync(kFull, base, 31);
+        long long r = ring_wrap(S.fe + (long long)base + (x - nfreed), P.cap);
+        for (int j = 0; j < nfreed; j++) {
+            P.ring[r] = freed[j];
+            if (++r == P.cap) r = 0;
         }
     }
-    unsigned long long x = frees, y = left;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_down_sync(kFull, x, o);
-        y += __shfl_down_sync(kFull, y, o);
+        frees += __shfl_down_sync(kFull, frees, o);
+        left += __shfl_down_sync(kFull, left, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (x) atomicAdd(&A->gc_frees, x);
-        if (y) atomicAdd(&A->gc_deaths, y);
+    if (lane == 0) {
+        if (frees) atomicAdd(&A->gc_frees, frees);
+        if (left) atomicAdd(&A->gc_deaths, left);
     }
 }
 

@@ -71,9 +71,11 @@ struct Program {
 struct Acc {  // per-sweep accumulators, triple-buffered by sweep number % 3
     unsigned long long rewrites, nf_marks, visits, allocs;
     unsigned long long fl_claims;  // allocation positions claimed in this sweep
-    unsigned long long deaths;     // reference counts that reached zero
+    unsigned long long deaths;     // reference decrements (each a possible death)
     unsigned long long pushes;     // entries written to the next frontier
-    unsigned long long gc_frees, gc_deaths, gc_append;  // garbage collection
+    unsigned long long gc_frees, gc_deaths, gc_append;  // garbage collection: freed, dead ones
+                                                        // left for the next one, ring appends
+    unsigned long long gc_cand;    // garbage collection: candidates taken from the bitmap
     unsigned long long conf_found, refresh_sel;
     unsigned long long taken;      // eager frontier sweep: entries claimed
     unsigned long long pending;    // learned refresh: live nodes not in normal form
@@ -86,7 +88,8 @@ struct Ctl {
     long long n_top;      // high-water mark: slots [1, n_top) have been used
     long long fl_begin;   // free ring: positions [fl_begin, fl_end) hold free slots
     long long fl_end;
-    long long dead;       // nodes with reference count 0 not yet reclaimed
+    long long dead;       // reference decrements since the last collection (an upper
+                          // bound of the dead nodes not yet reclaimed)
     long long fq_size;    // entries in the current frontier
     int fq_cur;           // which frontier buffer is current
     int status;           // trs_status of the device run
@@ -94,6 +97,7 @@ struct Ctl {
     int gc_pending;       // graph / host drivers: collect before the next sweep
     int mode_phase;       // 1 = seed the frontier at the next launch
     int solo_flags;       // outcome of the last solo episode: done | gc << 1 | confirm << 2 | stop << 3
+    int pad0, pad2;
     long long solo_ran;   // sweeps run by the last solo episode
     // statistics of the current trs_normalize
     long long st_rewrites, st_nf_marks, st_sweeps, st_visits, st_allocs, st_frees;
@@ -131,6 +135,9 @@ struct DevPool {
     int32_t *ring;  // free ring, cap entries, position p at ring[p % cap]
     int32_t *fq[2]; // frontier buffers
     int32_t *act;   // predictor traces: first sweep a node acted after a sample
+    uint32_t *dbm;  // candidate bitmap (cap bits): set for a slot whose count was
+                    // decremented since the last collection (fire and forget)
+    int32_t *cand;  // collection: the candidates compacted from the bitmap
     trs_sweep_record *trace;
     Ctl *ctl;
     const int32_t *tab;  // compiled rule table

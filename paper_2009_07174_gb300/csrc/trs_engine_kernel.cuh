@@ -100,6 +100,10 @@ __device__ Flags end_sweep(State &S, const AccVals &V, const LaunchOpts &o, long
     S.n += claims > avail ? claims - avail : 0;
     S.fb += claims < avail ? claims : avail;
     S.fe += (long long)V.ret;
+    if (S.fb >= cap) {  // ring positions stay below 2 * cap
+        S.fb -= cap;
+        S.fe -= cap;
+    }
     if (S.n > cap) S.n = cap;
     S.dead += (long long)V.deaths;
     const bool action = V.rew + V.nfm > 0;
@@ -119,9 +123,9 @@ __device__ Flags end_sweep(State &S, const AccVals &V, const LaunchOpts &o, long
         F.stall = !action;
     }
     // collection trigger: the plain sweep scans every slot below the high-water
-    // mark, so it collects early (dead >= n / 8 by default) to keep the mark
-    // low; the frontier modes only pay for collection, so they collect when
-    // the dead estimate reaches the high-water mark itself (by default) or
+    // mark, so it collects early (decrements >= n / 8 by default) to keep the
+    // mark low; the frontier modes only pay for collection, so they collect
+    // when the decrements reach the high-water mark itself (by default) or
     // when fewer than cap / 8 slots remain free (above the mark or in the ring)
     const int div = o.gc_div > 0 ? o.gc_div : (o.mode == M_PLAIN ? 8 : 1);
     long long thr = (long long)o.gc_min_dead;
@@ -156,6 +160,10 @@ __device__ __forceinline__ void note_sweep(LocalStats &L, const AccVals &V, cons
         rec.visits = (int32_t)V.vis;
         rec.allocs = (int32_t)V.alc;
         rec.high_water = S.n;
+        rec.t_ns = now_ns() - ctl->t_start;
+        rec.frontier = (int32_t)(S.fsz < 0x7fffffff ? S.fsz : 0x7fffffff);
+        rec.flags = (solo ? TRS_SWEEP_SOLO : 0) | (F.gc ? TRS_SWEEP_GC : 0) |
+                    (F.confirm ? TRS_SWEEP_CONFIRM : 0) | (F.refresh ? TRS_SWEEP_REFRESH : 0);
     }
     if (F.stop) atomicCAS(&ctl->status, 0, TRS_ERR_SWEEP_LIMIT);
     if (now_ns() - ctl->t_start > o.time_limit_ns) atomicCAS(&ctl->status, 0, TRS_ERR_TIMEOUT);
@@ -318,7 +326,10 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
             if (t0) memset(&ctl->acc[(S.k + 1) % 3], 0, sizeof(Acc));
             Acc *A = &ctl->acc[S.k % 3];
             if (o.mode == M_PLAIN) phase_plain(P, T, S, A, gw0, gnw);
-            else phase_frontier(P, T, S, A, o.mode, gw0, gnw, o.eager);
+            else {
+                const bool narrow = o.eager > 0 && S.fsz <= gnw;
+                phase_frontier(P, T, S, A, o.mode, gw0, gnw, o.eager, narrow, narrow);
+            }
             if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
             const AccVals V = read_acc(A, false);
             F = end_sweep(S, V, o, P.cap);
@@ -330,7 +341,10 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
         // ---- garbage collection between sweeps
         if (F.gc) {
             Acc *A = &ctl->acc[S.k % 3];
-            phase_gc(P, T, S, A, blockIdx.x, gridDim.x);
+            phase_gc_collect(P, S, A, gw0, gnw);
+            if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
+            const long long ncand = (long long)read_u64_block(&A->gc_cand);
+            phase_gc_free(P, T, S, A, ncand, gw0, gnw);
             if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
             __shared__ unsigned long long s_gc[3];
             if (threadIdx.x == 0) {
@@ -340,8 +354,8 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
             }
             __syncthreads();
             S.fe += (long long)s_gc[0];
-            // every dead node below the high-water mark was freed, except
-            // those whose count reached 0 during this pass
+            // every candidate whose count was 0 was freed with the nodes it
+            // killed; dead nodes the walks left are marked for the next one
             S.dead = (long long)s_gc[1];
             if (t0) {
                 L.gc_runs += 1;

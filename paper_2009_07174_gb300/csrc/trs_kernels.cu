@@ -15,20 +15,30 @@
 
 namespace trs {
 
-// Unpin a root (term_release).
+// Unpin a root (term_release): the root becomes a collection candidate, and
+// the next collection frees the term if that was its last reference.
 __global__ void k_release(DevPool P, int32_t root)
 {
-    if (atomicSub(&rc_at(P, root), 1) == 1) atomicAdd((unsigned long long *)&P.ctl->dead, 1ull);
+    if (atomicSub(&rc_at(P, root), 1) == 1) {
+        P.dbm[root >> 5] |= 1u << (root & 31);
+        P.ctl->dead += 1;
+    }
 }
 
-// Slot 0 is the null node: never live, never free-listed.
+// Slot 0 is the null node: never live, never free-listed.  The candidate
+// bitmap starts empty.
 __global__ void k_reset(DevPool P)
 {
     Ctl *c = P.ctl;
-    c->sweep_id = 1;
-    c->n_top = 1;
-    for (int w = 0; w < P.rs; w++) P.rec[w] = 0;
-    P.nfs[0] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->sweep_id = 1;
+        c->n_top = 1;
+        for (int w = 0; w < P.rs; w++) P.rec[w] = 0;
+        P.nfs[0] = 0;
+    }
+    const long long nw = (P.cap + 31) / 32;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < nw; w += (long long)gridDim.x * blockDim.x)
+        P.dbm[w] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -87,7 +97,7 @@ cudaError_t release_launch(const DevPool &P, int32_t root, cudaStream_t stream)
 
 cudaError_t reset_launch(const DevPool &P, cudaStream_t stream)
 {
-    k_reset<<<1, 1, 0, stream>>>(P);
+    k_reset<<<256, 256, 0, stream>>>(P);
     return cudaGetLastError();
 }
 

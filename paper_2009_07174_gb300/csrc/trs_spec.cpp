@@ -156,6 +156,28 @@ ReusePlan reuse_plan(const RuleView &r)
 }
 
 
+// Arguments whose records the decision for head h loads (their heads or
+// second-level words appear in h's patterns, or their counts decide a slot
+// reuse).  When a rewrite makes a node of head h its continuation, the
+// records of these arguments are prefetched, so that the next step's
+// dependent load hits L1.
+std::set<int> inspected_args(const Program &P, int h)
+{
+    std::set<int> out;
+    if (h <= 0 || h >= P.nsym) return out;
+    const int32_t *first = P.table.data() + P.table[5];
+    for (int s = first[h]; s < first[h + 1]; s++) {
+        const RuleView r = rule_view(P, s);
+        const std::vector<PatNode> ns = pattern_nodes(r);
+        for (size_t q = 1; q < ns.size(); q++) {
+            if (ns[q].path.size() == 1 && ns[q].sym) out.insert(ns[q].path[0]);
+            if (ns[q].path.size() == 2 && ns[q].path[1] < 3) out.insert(ns[q].path[0]);
+        }
+        for (int q : reuse_plan(r).cand) out.insert(ns[q].argpos);
+    }
+    return out;
+}
+
 void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, int last)
 {
     const int ar = arity_of(P, h);
@@ -166,7 +188,7 @@ void gen_decide_head(std::ostringstream &o, const Program &P, int h, int first, 
     }
     if (ar > 0) {
         o << "        if (check_ready) {\n            bool ready = true;\n";
-        for (int j = 0; j < ar; j++) o << "            ready &= is_nf_at(P.nfs[c" << j << "], k);\n";
+        for (int j = 0; j < ar; j++) o << "            ready &= nf_ready(P, c" << j << ", k, check_ready);\n";
         o << "            if (!ready) return D_SKIP;\n        }\n";
     }
     // every pattern node of every rule of h, by path
@@ -261,6 +283,22 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
     auto opnd = [&](int32_t op) -> std::string {
         return (op >> 16) ? new_slot(op & 0xffff) : "reg[" + std::to_string(op & 0xffff) + "]";
     };
+    // the content of a node that becomes the eager continuation (its
+    // arguments' records are prefetched for the next step)
+    auto emit_carry = [&](const std::string &ind, int sym, const std::vector<std::string> &ops) {
+        const int na = (int)ops.size();
+        for (int a : inspected_args(P, sym))
+            if (a < na) o << ind << "prefetch_rec(P, " << ops[a] << ");\n";
+        if (na <= 4) {
+            o << ind << "last.h = " << sym << ";\n";
+            for (int a = 0; a < na; a++) o << ind << "last.c[" << a << "] = " << ops[a] << ";\n";
+        } else {
+            o << ind << "last.h = 0;\n";
+        }
+    };
+    // learned mode queues the nodes a rewrite makes ready, the eager
+    // continuation last; a redex that waits for new arguments is queued by
+    // the last of them to become a normal form
     for (int j = 0; j < r.nnew; j++) {
         const int32_t w0 = r.build[pos++], w1 = r.build[pos++];
         const int sym = w0 & 0xffff, na = w0 >> 16;
@@ -294,16 +332,13 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
             o << "            reinterpret_cast<int4 *>(node_at(P, x))[" << q / 4 << "] = make_int4(" << w[q] << ", "
               << w[q + 1] << ", " << w[q + 2] << ", " << w[q + 3] << ");\n";
         o << "            P.nfs[x] = stamp_new;\n";
-        o << "            if (mode == M_LEARNED) {\n                push[npush++] = x;\n                last.h = 0;\n"
-             "            } else {\n";
+        o << "            if (mode == M_LEARNED) {\n                push[npush++] = x;\n";
+        if (pj == 0) emit_carry("                ", sym, ops);
+        else o << "                last.h = 0;\n";
+        o << "            } else {\n";
         if (pj == 0) {
             o << "                if (mode == M_FRONTIER) {\n                    push[npush++] = x;\n";
-            if (na <= 4) {
-                o << "                    last.h = " << sym << ";\n";
-                for (int a = 0; a < na; a++) o << "                    last.c[" << a << "] = " << ops[a] << ";\n";
-            } else {
-                o << "                    last.h = 0;\n";
-            }
+            emit_carry("                    ", sym, ops);
             o << "                }\n";
         }
         o << "            }\n        }\n";
@@ -319,22 +354,21 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
         o << "        const int xa = T.arity(xh);\n";
         for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) red_add_s32(&rc_at(P, xc" << a << "), 1);\n";
     }
-    int deaths = 0;
     std::vector<std::pair<int, int>> deltas;
     if (rp) {
         deltas = rp->delta;
     } else {
         for (int d = 0; d < r.ndelta; d++) deltas.push_back({r.delta[d] & 0xff, r.delta[d] >> 8});
     }
+    // fire and forget: a decremented node becomes a collection candidate
     for (auto &e : deltas) {
         o << "        red_add_s32(&rc_at(P, reg[" << e.first << "]), " << e.second << ");\n";
-        if (e.second < 0) deaths++;
+        if (e.second < 0) o << "        mark_candidate(P, reg[" << e.first << "], C);\n";
     }
-    if (deaths) o << "        C.deaths += " << deaths << ";\n";
     if (r.rootvar) {
         o << "        hs_at(P, i) = xh;\n";
         for (int a = 0; a < ma; a++) o << "        if (" << a << " < xa) arg_at(P, " << a << ", i) = xc" << a << ";\n";
-        o << "        P.nfs[i] = (int32_t)(k + 1);\n        {\n            const int before = npush;\n"
+        o << "        store_nf(P, mode, i, k);\n        {\n            const int before = npush;\n"
              "            if (mode == M_FRONTIER) notify_parent(P, pv, push, npush);\n"
              "            if (mode == M_LEARNED) {\n                const int32_t p = pv & 0x7fffffff;\n"
              "                if (p != 0) learned_push(P, p, k + 1, push, npush);\n            }\n"
@@ -346,16 +380,17 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
             ops.push_back(opnd(r.build[a]));
             o << "        arg_at(P, " << a << ", i) = " << ops.back() << ";\n";
         }
-        o << "        if (mode == M_LEARNED) {\n            learned_push(P, i, k + 1, push, npush);\n"
-             "            last.h = 0;\n        } else {\n            pend_at(P, i) = " << r.root_pend << ";\n";
+        o << "        if (mode == M_LEARNED) {\n";
+        if (r.root_pend == 0) {
+            o << "            const int before = npush;\n            learned_push(P, i, k + 1, push, npush);\n"
+                 "            last.h = 0;\n            if (npush != before) {\n";
+            emit_carry("                ", r.rootval, ops);
+            o << "            }\n";
+        }
+        o << "        } else {\n            pend_at(P, i) = " << r.root_pend << ";\n";
         if (r.root_pend == 0) {
             o << "            if (mode == M_FRONTIER) {\n                push[npush++] = i;\n";
-            if (r.root_nargs <= 4) {
-                o << "                last.h = " << r.rootval << ";\n";
-                for (int a = 0; a < r.root_nargs; a++) o << "                last.c[" << a << "] = " << ops[a] << ";\n";
-            } else {
-                o << "                last.h = 0;\n";
-            }
+            emit_carry("                ", r.rootval, ops);
             o << "            }\n";
         }
         o << "        }\n";
@@ -388,7 +423,7 @@ std::string generate(const Program &P)
     o << "// generated from the rule tables: " << P.nrules << " rules over " << P.nsym - 1 << " symbols\n";
     o << "namespace trs {\n\n";
     o << "__device__ __forceinline__ int spec_decide(const DevPool &P, const Tab &T, int32_t i, long long k,\n"
-         "                                           bool check_ready, int32_t *reg, int32_t &h_out,\n"
+         "                                           int check_ready, int32_t *reg, int32_t &h_out,\n"
          "                                           const Carry &cin)\n{\n";
     o << "    const long long cap = P.cap;\n    int32_t h;\n";
     for (int j = 0; j < 4; j++) o << "    int32_t w" << j << " = 0;\n";
@@ -407,7 +442,7 @@ std::string generate(const Program &P)
     o << "    if (check_ready) {\n        const int ar = T.arity(h);\n        bool ready = true;\n";
     for (int j = 0; j < P.maxarity; j++) {
         const std::string w = j < 4 ? "w" + std::to_string(j) : "arg_at(P, " + std::to_string(j) + ", i)";
-        o << "        if (" << j << " < ar) ready &= is_nf_at(P.nfs[" << w << "], k);\n";
+        o << "        if (" << j << " < ar) ready &= nf_ready(P, " << w << ", k, check_ready);\n";
     }
     o << "        if (!ready) return D_SKIP;\n    }\n    return D_MARK;\n}\n\n";
 

@@ -55,9 +55,11 @@ long long carve(unsigned char *base, const Program &p, DevPool *d)
     d->tab_words = (int32_t)p.table.size();
     off = up(off + p.table.size() * sizeof(int32_t));
     const int rs = rec_stride(p.maxarity);
-    const int words = rs + 4;  // record, nfs, ring, fq0, fq1 (the frontier buffers double as stacks)
-    if (off + (size_t)5 * 256 >= kStaticBytes) return 0;
-    long long cap = (long long)((kStaticBytes - off - (size_t)5 * 256) / ((size_t)words * 4));
+    // record, nfs, ring, fq0, fq1 (the frontier buffers double as stacks), the
+    // collection's candidate list; and one bit per slot (candidate bitmap)
+    const int words = rs + 6;
+    if (off + (size_t)7 * 256 >= kStaticBytes) return 0;
+    long long cap = (long long)((kStaticBytes - off - (size_t)7 * 256) * 8 / ((size_t)words * 32 + 1));
     cap = cap / 64 * 64;
     auto take = [&](size_t n) { unsigned char *at = base + off; off = up(off + n); return (int32_t *)at; };
     const size_t s = (size_t)cap * 4;
@@ -67,6 +69,8 @@ long long carve(unsigned char *base, const Program &p, DevPool *d)
     d->ring = take(s);
     d->fq[0] = take(s);
     d->fq[1] = take(s);
+    d->cand = take(s);
+    d->dbm = (uint32_t *)take((size_t)(cap + 31) / 32 * 4);
     d->act = nullptr;
     d->cap = cap;
     d->ma = p.maxarity;
@@ -103,6 +107,8 @@ __global__ void k_static_upload(DevPool P, const int32_t *term, long long len, i
         if ((ar[s] & 0xff) > 0) { stk_node[sp] = node; stk_next[sp] = 0; sp++; }
     }
     if (sp != 0) { c->status = TRS_ERR_BAD_TERM; return; }
+    // candidate bits a previous call left below the new high-water mark
+    for (long long w = 0; w <= len / 32; w++) P.dbm[w] = 0;
     c->sweep_id = 1;
     c->n_top = len + 1;
     c->fl_begin = c->fl_end = 0;

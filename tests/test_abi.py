@@ -91,10 +91,35 @@ def test_pool_bytes_scale(trs):
     assert trs.lib.trs_pool_bytes(p._h, 1 << 21, ctypes.byref(b2)) == 0
     per_slot = (b2.value - b1.value) / (1 << 20)
     # 32-byte node record (head, 2 arguments, parent, count, pending, padding)
-    # + stamp + ring + 2 frontier buffers + trace
-    assert per_slot == 52
+    # + stamp + ring + 2 frontier buffers + trace + candidate list + candidate bit
+    assert per_slot == 56.125
     p5 = trs.trs_compile(ti.MSORT)   # arity 5: a 64-byte record
     assert trs.lib.trs_pool_bytes(p5._h, 1 << 20, ctypes.byref(b1)) == 0
     assert trs.lib.trs_pool_bytes(p5._h, 1 << 21, ctypes.byref(b2)) == 0
-    assert (b2.value - b1.value) / (1 << 20) == 84
+    assert (b2.value - b1.value) / (1 << 20) == 88.125
     assert trs.lib.trs_pool_bytes(p._h, 1, ctypes.byref(b1)) == trs.CODE["TRS_ERR_ARG"]
+
+
+def test_static_binding_rejects_bad_tensors(trs):
+    """trs_normalize_static passes raw data pointers to the C call, so the
+    binding refuses, before any GPU work, tensors the call would misread:
+    another element type, a strided view, a missing length element, or host
+    memory (the GPU would fault on a host pointer)."""
+    torch = pytest.importorskip("torch")
+    prog = trs.trs_compile(ti.FIB)
+    term = torch.tensor(ti.fib_term(5), dtype=torch.int32)
+    out = torch.zeros(64, dtype=torch.int32)
+    n = torch.zeros(1, dtype=torch.int64)
+    cases = [
+        ((term.to(torch.int64), out, n), TypeError, "dtype"),
+        ((term, out.to(torch.float32), n), TypeError, "dtype"),
+        ((term, out, n.to(torch.int32)), TypeError, "dtype"),
+        ((term, out[::2], n), ValueError, "contiguous"),
+        ((term[:0], out, n), ValueError, "at least"),
+        ((term, out, n[:0]), ValueError, "at least"),
+        ((term, out, n), ValueError, "CUDA"),
+        ((list(ti.fib_term(5)), out, n), TypeError, "torch.Tensor"),
+    ]
+    for args, exc, words in cases:
+        with pytest.raises(exc, match=words):
+            trs.trs_normalize_static(prog, *args)

@@ -29,16 +29,12 @@ def test_profiled_traffic_reads_committed_records(bench):
     smaller case is scaled by the units it processed."""
     d = os.path.join(ROOT, "profiles")
     current = bench.kernel_source_hash()
-    for name in ("k_engine_fib22_frontier", "k_engine_plain_scan"):
+    for name in ("k_engine_fib22_frontier",):
         text = open(os.path.join(d, name + ".md")).read()
         assert "source_sha256" in text and "traffic_bytes_per_launch" in text
         if current in text:
             t = bench.profiled_traffic(name)
             assert t is not None and t > 0
-    if current in open(os.path.join(d, "k_engine_plain_scan.md")).read():
-        one = bench.profiled_traffic("k_engine_plain_scan")
-        two = bench.profiled_traffic("k_engine_plain_scan", units=2 * 54159727)
-        assert abs(two - 2 * one) <= 2
 
 
 def test_profiled_traffic_is_none_for_other_sources(bench, tmp_path, monkeypatch):
@@ -56,19 +52,18 @@ def test_profiled_traffic_is_none_for_other_sources(bench, tmp_path, monkeypatch
 
 
 def test_alg_bytes_counts_every_term(bench):
-    st = {"mode": "frontier", "visits": 10, "rewrites": 4, "allocs": 3, "nf_marks": 5, "frees": 2,
+    st = {"visits": 10, "rewrites": 4, "allocs": 3, "nf_marks": 5, "frees": 2,
           "gc_runs": 1, "high_water": 100, "confirm_sweeps": 1}
-    b0 = bench.alg_bytes(st, None, 2)
+    b0 = bench.alg_bytes(st, None, 2, "frontier")
     # maxarity 2: a node is 12 bytes (head and two arguments)
-    want = 10 * (12 + 8 + 4) + 4 * (12 + 16 + 12) + 3 * (12 + 16) + 5 * 8 + (100 * 8 + 2 * 16) \
+    want = 10 * (12 + 8 + 4) + 4 * (12 + 16 + 12) + 3 * (12 + 16) + 5 * 8 + 2 * (4 + 12 + 4 + 4) \
         + 2 * 100 * 4 + 10 * 8
     assert b0 == want
     for k in ("visits", "rewrites", "allocs", "nf_marks", "frees"):
-        assert bench.alg_bytes(dict(st, **{k: st[k] + 1}), None, 2) > b0
+        assert bench.alg_bytes(dict(st, **{k: st[k] + 1}), None, 2, "frontier") > b0
     # the plain sweep adds 4 bytes per slot of every sweep's scan (trace column 5)
-    plain = dict(st, mode="plain")
-    assert bench.alg_bytes(plain, [(0, 0, 0, 0, 0, 50), (1, 0, 0, 0, 0, 70)], 2) == \
-        bench.alg_bytes(plain, None, 2) + 120 * 4
+    assert bench.alg_bytes(st, [(0, 0, 0, 0, 0, 50), (1, 0, 0, 0, 0, 70)], 2, "plain") == \
+        bench.alg_bytes(st, None, 2, "plain") + 120 * 4
 
 
 def test_reference_arm_line(tmp_path):

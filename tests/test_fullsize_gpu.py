@@ -165,3 +165,31 @@ def test_ttree22_paper_headline(trs, spec):
         assert np.array_equal(got, expect), kw
         if not kw.get("eager"):
             assert st["sweeps"] == 3 * n + 29
+
+
+def test_tree_merge_sort_23_5(trs):
+    """Tree merge sort 23 5 at paper scale (Sec. 4, Table 2): 2^23 lists of 5
+    numerals 0..9 in the leaves of a complete Node tree, one term of about
+    306M symbols, pool 2^30 slots.  Every leaf of the normal form is its list
+    sorted (the whole serialisation equals the input tree with the lists
+    sorted and the Sort symbols gone), and the rewrite total equals the sum,
+    over the lists, of the oracle's count for Sort of that list (Leaf and Node
+    have no rules), taken once per distinct list."""
+    t = ti.MSORT
+    term, vals = ti.msort_uniform_batch(depth=23, length=5)
+    uniq, counts = np.unique(vals, axis=0, return_counts=True)
+    o = Oracle(t)
+    total = 0
+    for row, c in zip(uniq, counts):
+        total += int(c) * o.normalize(ti.msort_tree_uniform(row[None, :])).rewrites
+    prog = program(trs, t, True)
+    pool = trs.Pool(prog, 1 << 30)
+    r = pool.term_upload(term)
+    del term
+    st = pool.trs_normalize(**trs.autotune_defaults("frontier", "msort"))
+    assert st["status"] == 0 and st["rewrites"] == total
+    got = pool.term_download(r)
+    del pool
+    want = ti.msort_tree_uniform(np.sort(vals, axis=1))
+    want = want[want != t.id["Sort"]]
+    assert len(got) == len(want) and np.array_equal(got, want)

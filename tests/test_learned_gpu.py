@@ -302,3 +302,133 @@ def test_learned_mode_progress_with_waiting_only_predictor(env, spec):
     for g, w in zip(pool.term_download_batch(roots), want):
         assert np.array_equal(g, w.term)
     assert st["rewrites"] == sum(w.rewrites for w in want)
+
+
+def _learned_terms(t):
+    if t is ti.FIB:
+        return [ti.fib_term(n) for n in (0, 3, 11, 17)], [ti.fib_term(n) for n in range(8, 17)]
+    if t is ti.ARITH:
+        terms = ti.split_terms(*ti.arith_batch(seed=2, count=30, dmin=2, dmax=6)[:2])
+        return terms, terms
+    terms = [ti.msort_batch(seed=3, nlists=4, lmin=2, lmax=30, vmax=9)[0]]
+    return terms, terms
+
+
+@pytest.mark.parametrize("spec", [False, True], ids=["table-driven", "specialised"])
+@pytest.mark.parametrize("t", [ti.FIB, ti.ARITH, ti.MSORT], ids=["fib", "arith", "msort"])
+def test_learned_eager_is_exact(env, t, spec):
+    """The learned frontier with eager continuation (a lane goes on with a
+    node it made ready, checked against the current state) and solo
+    episodes: for any selection (everything, the trained choice, nothing) the
+    normal forms and the rewrite and normal-form-mark counts are the
+    oracle's."""
+    torch, trs = env
+    prog = trs.trs_compile(t)
+    if spec:
+        prog.specialise()
+    terms, train = _learned_terms(t)
+    pred = trained_predictor(torch, trs, prog, t, train, period=8)
+    o = Oracle(t)
+    want = [o.normalize(x) for x in terms]
+    flat, offs = ti.concat_terms(terms)
+    for thr in (0.0, 0.5, 1.01):
+        for kw in (dict(eager=16, solo_max=0), dict(eager=256, solo_max=512)):
+            pool = trs.Pool(prog, 1 << 22)
+            pool.trs_pool_attach_predictor(pred)
+            roots = pool.term_upload_batch(flat, offs)
+            st = pool.trs_normalize(mode="learned", threshold=thr, refresh=16, **kw)
+            assert st["specialised"] == int(spec)
+            for g, w in zip(pool.term_download_batch(roots), want):
+                assert np.array_equal(g, w.term), (thr, kw)
+            assert st["rewrites"] == sum(w.rewrites for w in want), (thr, kw)
+            assert st["nf_marks"] == sum(w.nf_marks for w in want), (thr, kw)
+
+
+@pytest.fixture(scope="module")
+def fib_pred(env):
+    torch, trs = env
+    from paper_2009_07174_gb300 import learn
+    prog = trs.trs_compile(ti.FIB).specialise()
+    flat, offs = ti.concat_terms([ti.fib_term(n) for n in range(8, 21)])
+    return prog, learn.train_for(prog, flat, offs, 1 << 24, period=16)
+
+
+@pytest.mark.parametrize("eager", [0, 256])
+def test_learned_fib22_full_size(env, fib_pred, eager):
+    """fib(22) in a pool of 2^24 slots in learned mode with the benchmark's
+    predictor (trained on the engine's traces of fib(8) .. fib(20)), the
+    synchronous sweep and the eager one: S^17711(0), 186,579 rewrites and
+    175,657 normal-form marks, as the oracle."""
+    torch, trs = env
+    from paper_2009_07174_gb300 import autotune_defaults
+    prog, pred = fib_pred
+    want = Oracle(ti.FIB).normalize(ti.fib_term(22))
+    pool = trs.Pool(prog, 1 << 24)
+    pool.trs_pool_attach_predictor(pred)
+    r = pool.term_upload(ti.fib_term(22))
+    kw = dict(autotune_defaults("learned", "fib22"), eager=eager)
+    st = pool.trs_normalize(**kw)
+    assert np.array_equal(pool.term_download(r), want.term)
+    assert st["rewrites"] == want.rewrites == 186579
+    assert st["nf_marks"] == want.nf_marks == 175657
+
+
+@pytest.mark.parametrize("eager", [0, 256])
+def test_config5_learned_full_size(env, eager):
+    """Config 5 as stated: merge sort of 256 seeded lists (64..1024 numerals
+    0..31) in learned mode, the predictor trained on the engine's own traces
+    of a smaller merge-sort batch: every leaf sorted, and normal form and
+    counts equal to the oracle's."""
+    torch, trs = env
+    from paper_2009_07174_gb300 import autotune_defaults, learn
+    t = ti.MSORT
+    prog = trs.trs_compile(t).specialise()
+    flat, offs = ti.concat_terms([ti.msort_batch(seed=7, nlists=16, lmin=64, lmax=256)[0]])
+    pred = learn.train_for(prog, flat, offs, 1 << 22, period=16)
+    term, lists = ti.msort_batch(seed=0)
+    want = Oracle(t).normalize(term)
+    expect = ti.msort_tree([sorted(l) for l in lists])
+    expect = expect[expect != t.id["Sort"]]
+    assert np.array_equal(want.term, expect)
+    pool = trs.Pool(prog, 1 << 24)
+    pool.trs_pool_attach_predictor(pred)
+    r = pool.term_upload(term)
+    st = pool.trs_normalize(**dict(autotune_defaults("learned", "msort"), eager=eager))
+    assert np.array_equal(pool.term_download(r), expect)
+    assert st["rewrites"] == want.rewrites and st["nf_marks"] == want.nf_marks
+
+
+def test_learned_against_exact_frontier_and_plain(env, fib_pred, record_property):
+    """What the trained network gains, measured on fib(20): the plain
+    all-node sweep (the method without any frontier) examines every pending
+    node every sweep; the learned frontier examines a small fraction of
+    that.  The exact frontier (parent pointers and pending counts, no
+    network) examines exactly the nodes that act, the least any frontier can
+    visit, so the network cannot visit fewer: the test records all three."""
+    torch, trs = env
+    prog, pred = fib_pred
+    res = {}
+    for name, kw in (("plain", dict(mode="plain")), ("learned", dict(mode="learned", refresh=16, threshold=0.5)),
+                     ("learned_eager", dict(mode="learned", refresh=16, threshold=0.5, eager=256, solo_max=512)),
+                     ("frontier", dict(mode="frontier")),
+                     ("frontier_eager", dict(mode="frontier", eager=256, solo_max=512))):
+        pool = trs.Pool(prog, 1 << 22)
+        pool.trs_pool_attach_predictor(pred)
+        r = pool.term_upload(ti.fib_term(20))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pool.trs_normalize(wait=False, **kw)
+        e1.record()
+        e1.synchronize()
+        st = pool.trs_pool_stats()
+        res[name] = {"visits": st["visits"], "sweeps": st["sweeps"], "ms": e0.elapsed_time(e1),
+                     "term": pool.term_download(r)}
+    for k in res:
+        assert np.array_equal(res[k]["term"], res["plain"]["term"])
+        record_property(k, {kk: v for kk, v in res[k].items() if kk != "term"})
+    acted = 67526 + Oracle(ti.FIB).normalize(ti.fib_term(20)).nf_marks
+    assert res["frontier"]["visits"] == acted        # exactly the nodes that act
+    assert res["learned"]["visits"] >= acted
+    assert res["learned"]["visits"] < 0.5 * res["plain"]["visits"]
+    assert res["learned_eager"]["sweeps"] < res["learned"]["sweeps"]

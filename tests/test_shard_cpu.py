@@ -75,3 +75,64 @@ def test_two_rank_gloo_matches_single_process():
     want = [orc.normalize(t) for t in ti.split_terms(flat, offs)]
     assert [list(w.term) for w in want] == terms
     assert tot == {"rewrites": sum(w.rewrites for w in want), "terms": 60}
+
+
+class _OracleStats:
+    """A rank-local stand-in for the GPU normaliser (the CPU oracle, with the
+    same result shape), so that partition, gather and ordering of
+    normalize_sharded are checked on the product code without a GPU."""
+
+    def __init__(self, t):
+        from oracle import Oracle
+        self.o = Oracle(t)
+        self.calls = 0
+
+    def __call__(self, flat, offs):
+        self.calls += 1
+        res = [self.o.normalize(flat[offs[i]:offs[i + 1]]) for i in range(len(offs) - 1)]
+        st = {"rewrites": sum(r.rewrites for r in res), "nf_marks": sum(r.nf_marks for r in res),
+              "allocs": 0, "frees": 0, "visits": 0}
+        return [r.term for r in res], st
+
+
+def _sharded_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    from paper_2009_07174_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        flat, offs, meta = ti.arith_batch(seed=5, count=40, dmin=2, dmax=6)
+        fake = _OracleStats(ti.ARITH)
+        out, tot = shard.normalize_sharded(flat, offs, shard.arith_costs(meta), fake)
+        q.put((rank, [list(map(int, x)) for x in out], tot, fake.calls))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_normalize_sharded_two_ranks_gloo():
+    """normalize_sharded with 2 gloo ranks: every rank gets every normal form
+    back in the batch's order and the summed counters, equal to one process
+    normalising the whole batch."""
+    import torch.multiprocessing as mp
+
+    from oracle import Oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    flat, offs, meta = ti.arith_batch(seed=5, count=40, dmin=2, dmax=6)
+    orc = Oracle(ti.ARITH)
+    want = [orc.normalize(t) for t in ti.split_terms(flat, offs)]
+    for rank, terms, tot, calls in got:
+        assert terms == [list(map(int, w.term)) for w in want]
+        assert tot["rewrites"] == sum(w.rewrites for w in want)
+        assert tot["nf_marks"] == sum(w.nf_marks for w in want)
+        assert calls == 1

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import trs_inputs as ti
+from oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -58,9 +59,12 @@ def test_static_matches_pool_two_calls(env, mode, spec):
         if spec:
             prog.specialise()
         want, st_want = via_pool(trs, prog, term, mode)
+        oracle = Oracle(t).normalize(term)
+        assert np.array_equal(want, oracle.term)
         for _ in range(2):       # two calls in a row share the array
             got, st = via_static(torch, trs, prog, term, mode)
-            assert np.array_equal(got, want)
+            assert np.array_equal(got, oracle.term)
+            assert st["rewrites"] == oracle.rewrites and st["nf_marks"] == oracle.nf_marks
             assert st["specialised"] == int(spec) == st_want["specialised"]
             for k in ("rewrites", "nf_marks", "sweeps", "allocs"):
                 assert st[k] == st_want[k], (k, st, st_want)
@@ -75,3 +79,45 @@ def test_static_rejects_oversized_term(env):
     with pytest.raises(trs.TrsError) as e:
         trs.trs_normalize_static(prog, big, out, n)
     assert e.value.name == "TRS_ERR_TOO_BIG"
+
+
+def static_call(torch, trs, prog, term, out_cap):
+    d_term = torch.from_numpy(np.ascontiguousarray(term, dtype=np.int32)).cuda()
+    d_out = torch.full((max(out_cap, 1),), -7, dtype=torch.int32, device="cuda")
+    d_len = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
+    code = trs.lib.trs_normalize_static(prog._h, d_term.data_ptr(), d_term.numel(), d_out.data_ptr(),
+                                        out_cap, d_len.data_ptr(), None, None,
+                                        torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return code, int(d_len.item()), d_out
+
+
+@pytest.mark.parametrize("spec", [False, True])
+def test_static_device_errors_then_clean_call(env, spec):
+    """Errors found on the device leave the shared array reusable: a
+    malformed preorder (an unknown symbol, a truncated term, trailing
+    symbols) gives TRS_ERR_BAD_TERM with length 0, an output buffer shorter
+    than the normal form gives TRS_ERR_BUFFER_SMALL with length -1; the call
+    after each one returns the oracle's normal form."""
+    torch, trs = env
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    if spec:
+        prog.specialise()
+    good = ti.fib_term(12)
+    want = Oracle(t).normalize(good).term
+    S, Z, fib, plus = t.id["S"], t.id["0"], t.id["fib"], t.id["plus"]
+    bad_terms = [
+        np.array([fib, S, 999, Z], np.int32),        # symbol id beyond the signature
+        np.array([plus, S, Z], np.int32),            # truncated: plus lacks an argument
+        np.array([S, Z, Z], np.int32),               # a trailing symbol after a complete term
+    ]
+    for bad in bad_terms:
+        code, n, _ = static_call(torch, trs, prog, bad, 1 << 12)
+        assert trs.STATUS[code] == "TRS_ERR_BAD_TERM" and n == 0, (bad, code, n)
+        code, n, out = static_call(torch, trs, prog, good, 1 << 12)
+        assert code == 0 and np.array_equal(out[:n].cpu().numpy(), want)
+    code, n, out = static_call(torch, trs, prog, good, len(want) - 1)
+    assert trs.STATUS[code] == "TRS_ERR_BUFFER_SMALL" and n == -1
+    code, n, out = static_call(torch, trs, prog, good, len(want))
+    assert code == 0 and n == len(want) and np.array_equal(out[:n].cpu().numpy(), want)
