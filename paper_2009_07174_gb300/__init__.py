@@ -308,9 +308,20 @@ class Pool:
         _check(lib.trs_pool_stats(self._h, ctypes.byref(st), _stream(stream)), "trs_pool_stats")
         return st.as_dict()
 
-    def term_download_batch(self, roots, cap: int | None = None, stream=None):
+    def term_download_batch(self, roots, cap: int | None = None, stream=None, out=None):
+        """Normal forms of `roots` (canonical preorders).  With `out` (a
+        contiguous int32 host array, e.g. a view of pinned memory, large
+        enough for all of them) the symbols are written there and views into
+        it are returned; otherwise a buffer is allocated and grown as needed."""
         roots = np.ascontiguousarray(roots, dtype=np.int32)
         n = len(roots)
+        if out is not None:
+            if not (isinstance(out, np.ndarray) and out.dtype == np.int32 and out.flags.c_contiguous):
+                raise TypeError("term_download_batch: out must be a contiguous int32 numpy array")
+            offs = np.zeros(n + 1, dtype=np.int64)
+            _check(lib.term_download_batch(self._h, _ptr(roots), n, _ptr(out), len(out), _ptr(offs),
+                                           _stream(stream)), "term_download_batch")
+            return [out[offs[i]:offs[i + 1]] for i in range(n)]
         cap = int(cap) if cap is not None else 1 << 16
         offs = np.zeros(n + 1, dtype=np.int64)
         while True:

@@ -629,10 +629,11 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         P.nfs[x] = stamp_new;
         par_at(P, x) = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
         if (mode == M_LEARNED) {
-            pend_at(P, x) = (int32_t)(k + 1);
-            push[npush++] = x;
-            last.h = 0;
+            // a new node that waits for new arguments is queued (and
+            // claimed) by the last of them to become a normal form
+            pend_at(P, x) = pj == 0 ? (int32_t)(k + 1) : 0;
             if (pj == 0) {
+                push[npush++] = x;
                 last = cx;
                 prefetch_args(P, T, sym, cx, na);
             }
@@ -1258,7 +1259,7 @@ __device__ __forceinline__ void phase_gc_free(const DevPool &P, const Tab &T, co
 // normalisation and, as the full confirmation sweep, whenever the frontier
 // becomes empty.
 __device__ __forceinline__ void phase_seed(const DevPool &P, const Tab &T, const State &S, Acc *A,
-                                           long long block0, long long nblocks)
+                                           long long block0, long long nblocks, int mode = M_FRONTIER)
 {
     __shared__ unsigned long long s_base;
     int32_t *buf = P.fq[S.cur];
@@ -1286,8 +1287,12 @@ __device__ __forceinline__ void phase_seed(const DevPool &P, const Tab &T, const
                 const int32_t c = arg_at(P, a, i);
                 if (!is_nf_at(P.nfs[c], S.k)) cnt++;
             }
-            pend_at(P, i) = cnt;
-            if (cnt == 0 && -(long long)sv[t] <= S.k) ready[nready++] = (int32_t)i;
+            const bool rdy = cnt == 0 && -(long long)sv[t] <= S.k;
+            // frontier mode: pending-argument count; learned mode: the queue
+            // tag of the sweep the ready nodes join
+            if (mode != M_LEARNED) pend_at(P, i) = cnt;
+            else if (rdy) pend_at(P, i) = (int32_t)S.k;
+            if (rdy) ready[nready++] = (int32_t)i;
         }
         int total = 0;
         const int off = block_scan_count(nready, &total);
@@ -1328,7 +1333,8 @@ __device__ __forceinline__ void node_features(const DevPool &P, const Tab &T, in
 
 // Learned-frontier refresh: score every live node that is not in normal form
 // with the predictor (BF16 weights in shared memory, FP32 accumulation) and
-// compact those at or above the threshold into the current frontier buffer.
+// append those at or above the threshold, not queued already, to the current
+// frontier buffer.
 // Counts all such nodes too: a refresh that finds none is the full sweep that
 // confirms termination.
 __device__ __forceinline__ void phase_refresh(const DevPool &P, const Tab &T, const MlpView &M, const State &S, Acc *A,
@@ -1352,14 +1358,18 @@ __device__ __forceinline__ void phase_refresh(const DevPool &P, const Tab &T, co
             for (int j = 0; j < TRS_MAX_ARITY; j++) a[j] = 0;
         }
         const float p = mlp_warp_prob(M, pending, h, a, bits);
-        const bool sel = pending && p >= thr;
+        // the selection joins the entries the last sweep queued (those carry
+        // this sweep's number in their pending word)
+        const bool sel = pending && p >= thr && pend_at(P, i) != (int32_t)S.k;
+        if (sel) pend_at(P, i) = (int32_t)S.k;
         pend += pending ? 1 : 0;
         int total = 0;
         const int off = block_scan_flag(sel, &total);
         if (total > 0) {
             if (threadIdx.x == 0) s_base = atomicAdd(&A->refresh_sel, (unsigned long long)total);
             __syncthreads();
-            if (sel && (long long)s_base + off < P.cap) buf[s_base + off] = (int32_t)i;
+            const long long at = S.fsz + (long long)s_base + off;
+            if (sel && at < P.cap) buf[at] = (int32_t)i;
             __syncthreads();
         }
     }

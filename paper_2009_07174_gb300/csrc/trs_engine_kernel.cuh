@@ -399,12 +399,12 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
             }
             S.since = 0;
             if (pend == 0) { finished = true; goto out; }  // a full scan found no work
-            S.fsz = sel;
-            if (sel == 0 || F.stall) {
-                // the predictor selected nothing, or its last frontier made no
+            S.fsz += sel;
+            if (S.fsz == 0 || F.stall) {
+                // nothing queued or selected, or the last frontier made no
                 // progress (it may hold only nodes that wait for others, and
                 // would be selected again): take the ready nodes instead
-                phase_seed(P, T, S, A, blockIdx.x, gridDim.x);
+                phase_seed(P, T, S, A, blockIdx.x, gridDim.x, M_LEARNED);
                 if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
                 S.fsz = (long long)read_u64_block(&A->conf_found);
                 if (t0) L.confirm_found += S.fsz;

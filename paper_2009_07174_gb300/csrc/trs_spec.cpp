@@ -327,14 +327,19 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
         for (int a = 0; a < na; a++) w[rec_arg(a)] = ops[a];
         w[rec_par(ma)] = "(" + parw + ")";
         w[rec_rc(ma)] = "1";
-        w[rec_pend(ma)] = "(mode == M_LEARNED ? (int32_t)(k + 1) : " + std::to_string(pj) + ")";
+        // learned mode: a node queued for the next sweep carries that sweep's
+        // number; one waiting for new arguments is queued by the last of them
+        w[rec_pend(ma)] = pj == 0 ? "(mode == M_LEARNED ? (int32_t)(k + 1) : 0)"
+                                  : "(mode == M_LEARNED ? 0 : " + std::to_string(pj) + ")";
         for (int q = 0; q < rs; q += 4)
             o << "            reinterpret_cast<int4 *>(node_at(P, x))[" << q / 4 << "] = make_int4(" << w[q] << ", "
               << w[q + 1] << ", " << w[q + 2] << ", " << w[q + 3] << ");\n";
         o << "            P.nfs[x] = stamp_new;\n";
-        o << "            if (mode == M_LEARNED) {\n                push[npush++] = x;\n";
-        if (pj == 0) emit_carry("                ", sym, ops);
-        else o << "                last.h = 0;\n";
+        o << "            if (mode == M_LEARNED) {\n";
+        if (pj == 0) {
+            o << "                push[npush++] = x;\n";
+            emit_carry("                ", sym, ops);
+        }
         o << "            } else {\n";
         if (pj == 0) {
             o << "                if (mode == M_FRONTIER) {\n                    push[npush++] = x;\n";

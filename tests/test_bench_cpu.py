@@ -24,15 +24,19 @@ def bench():
 
 
 def test_profiled_traffic_reads_committed_records(bench):
-    """Every committed engine summary names the kernel source it was taken
-    on; where that is the current source, its traffic is read back, and a
-    smaller case is scaled by the units it processed."""
+    """Every committed summary names the kernel source it was taken on and
+    the command that made it; where a traffic record's source is the current
+    one, its traffic is read back."""
+    import glob
     d = os.path.join(ROOT, "profiles")
     current = bench.kernel_source_hash()
-    for name in ("k_engine_fib22_frontier",):
-        text = open(os.path.join(d, name + ".md")).read()
-        assert "source_sha256" in text and "traffic_bytes_per_launch" in text
-        if current in text:
+    files = glob.glob(os.path.join(d, "*.md"))
+    assert files
+    for path in files:
+        text = open(path).read()
+        assert "source_sha256" in text and "```" in text, path
+        if "traffic_bytes_per_launch" in text and current in text:
+            name = os.path.splitext(os.path.basename(path))[0]
             t = bench.profiled_traffic(name)
             assert t is not None and t > 0
 
