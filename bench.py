@@ -74,6 +74,25 @@ def arith_rewrites(meta):
     return tot
 
 
+def arith_sweeps(meta):
+    """Sweeps of the synchronous parallel-innermost sweep over arithmetic
+    trees (the closed form the oracle is pinned to: a leaf S^v(0) is normal
+    from sweep v + 2, an operator ready at sweep r takes 2a + 1 more sweeps
+    for plus and 2 + 2a(b + 1) for times); the batch needs the maximum."""
+    out = 0
+    for d, ops, vals in meta:
+        nl = 1 << d
+        vis = np.zeros(2 * nl, dtype=np.int64)
+        vis[nl:] = vals[nl:2 * nl].astype(np.int64) + 2
+        for lvl in range(d - 1, -1, -1):
+            h = np.arange(1 << lvl, 1 << (lvl + 1))
+            a, b = vals[2 * h].astype(np.int64), vals[2 * h + 1].astype(np.int64)
+            ready = np.maximum(vis[2 * h], vis[2 * h + 1])
+            vis[h] = np.where(ops[h] == 1, ready + 2 + 2 * a * (b + 1), ready + 2 * a + 1)
+        out = max(out, int(vis[1] - 1))
+    return out
+
+
 def build_workload(name, seed=0):
     """(trs, flat, offsets, pool capacity, expected rewrites or None, description,
     autotune workload key, terms for the oracle sample)."""
@@ -96,6 +115,11 @@ def build_workload(name, seed=0):
         f, o = ti.concat_terms([term])
         return (ti.MSORT, f, o, 1 << 24, None,
                 "merge sort of 256 lists (64..1024 numerals 0..31), single term, pool 2^24", "msort")
+    if name == "tmsort23":
+        term, _ = ti.msort_uniform_batch(depth=23, length=5)
+        f, o = ti.concat_terms([term])
+        return (ti.MSORT, f, o, 1 << 30, None,
+                "tree merge sort 23 5: 2^23 lists of 5 numerals 0..9 in one Node tree, pool 2^30", "msort")
     if name == "ttree22":
         f, o = ti.concat_terms([ti.ttree_term(22)])
         return (ti.TTREE, f, o, 1 << 24, 28 * 2 ** 22 - 1,
@@ -103,7 +127,7 @@ def build_workload(name, seed=0):
     raise KeyError(name)
 
 
-CONFIGS = ["c1", "c2", "c3", "c4", "c5", "ttree22"]
+CONFIGS = ["c1", "c2", "c3", "c4", "c5", "ttree22", "tmsort23"]
 # launch options beyond the tuned ones (config 4 runs on the CUDA-graph driver)
 EXTRA = {"c4": {"driver": "graph", "graph_unroll": 4, "solo_max": 0}}
 
@@ -385,10 +409,21 @@ def config_block(name, spec_s, budget_s=60.0):
     big = r.cap >= (1 << 28)
     out["frontier"] = time_mode(r, r.opts("frontier"), 2 if big else 3)
     out["rewrites"] = out["frontier"].get("rewrites")
-    if name == "c3":
+    if name in ("c3", "tmsort23"):
         out["plain_sweep"] = plain_sampled(r, 40)
+        if name == "c3":
+            # the whole plain sweep: every sweep streams at least the input's
+            # stamps, 4 bytes per slot, at no more than the measured HBM peak
+            n = arith_sweeps(ti.arith_batch(seed=0, count=4096)[2])
+            peak, _ = peaks()
+            out["plain_sweep"]["sweeps_full"] = n
+            out["plain_sweep"]["ms_lower_bound_full"] = n * len(r.flat) * 4 / (peak * 1e9) * 1e3
     else:
         out["plain_sweep"] = time_mode(r, r.opts("plain"), 1)
+    if name == "tmsort23":       # the paper's tree merge sort; no learned run at this size
+        r.free()
+        torch.cuda.empty_cache()
+        return out
     # learned frontier: predictor trained on smaller terms of the same rules
     t0 = time.perf_counter()
     prog, pred, info = train_predictor(name)
@@ -530,6 +565,24 @@ def oracle_sample(name, target_s, threads=None):
     """Rewrites/s of the oracle on a bounded sample of workload `name`."""
     from oracle import Oracle, normalize_threads
     threads = threads or os.cpu_count() or 1
+    if name == "tmsort23":
+        # the tree's rewrites all happen inside its leaves: Leaf(Sort(list))
+        # of each list normalised as a term of its own, on a seeded sample
+        _, vals = ti.msort_uniform_batch(depth=23, length=5)
+        rng = np.random.default_rng(1)
+        pick = rng.choice(len(vals), 1 << 16, replace=False)
+        terms = [ti.msort_tree_uniform(vals[i][None, :]) for i in pick]
+        done, rew, t0 = 0, 0, time.perf_counter()
+        while done < len(terms):
+            res = normalize_threads(ti.MSORT, terms[done:done + 4096], threads)
+            rew += sum(x.rewrites for x in res)
+            done += len(res)
+            if time.perf_counter() - t0 >= target_s:
+                break
+        used = time.perf_counter() - t0
+        return {"value": rew / used, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": f"{done} of the 2^23 lists (seeded sample), each Leaf(Sort(list)) a term, "
+                          f"{threads} host threads", "seconds": used}
     t, flat, offs, _, _, _, _ = build_workload(name)
     nterms = len(offs) - 1
     terms = [flat[offs[i]:offs[i + 1]] for i in range(nterms)]

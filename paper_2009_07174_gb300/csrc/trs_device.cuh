@@ -693,14 +693,17 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
             if (a < kCarryArgs) ci.c[a] = v;
         }
         if (mode == M_LEARNED) {
+            // rewritten: eligible from the next sweep; the release store
+            // publishes the record for lanes that read the stamp with acquire
+            st_release_s32(&P.nfs[i], -(int32_t)(k + 1));
+            // the redex is this lane's: with every argument in normal form it
+            // is queued (or continued) without a claim; no argument event can
+            // target it (its arguments became normal forms before this step)
             if (root_pend == 0) {
-                const int before = npush;
-                learned_push(P, i, k + 1, push, npush);
-                last.h = 0;
-                if (npush != before) {
-                    last = ci;
-                    prefetch_args(P, T, R[1], ci, root_nargs);
-                }
+                pend_at(P, i) = (int32_t)(k + 1);
+                push[npush++] = i;
+                last = ci;
+                prefetch_args(P, T, R[1], ci, root_nargs);
             }
         } else {
             pend_at(P, i) = root_pend;
@@ -777,6 +780,18 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     // the parent word is loaded together with the node (it is needed when the
     // node turns out to be a normal form), not after the decision
     const int32_t pv = (mode != M_PLAIN && cand) ? par_at(P, i) : 0;
+    // learned mode with eager continuation: a frontier entry and a lane's
+    // claimed continuation can be the same node, so a lane owns a step only
+    // once it has swapped the node's stamp from the value it read before
+    // deciding to the step's outcome (-(k+1) rewritten, k+1 normal form); the
+    // acquire read pairs with the release stamp writes that follow a rewrite
+    // or a mark, so the record the decision reads is the one that stamp covers
+    const bool own = mode == M_LEARNED && eager && cand;
+    int32_t s_seen = 0;
+    if (own) {
+        s_seen = ld_acquire_s32(&P.nfs[i]);
+        if (s_seen > 0 || s_seen == 0 || (check_ready == R_SWEEP && -(long long)s_seen > S.k)) cand = false;
+    }
     if (cand) {
         C.visits++;
 #ifdef TRS_JIT
@@ -784,14 +799,21 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
 #else
         d = decide(P, T, i, S.k, check_ready, reg, h, carry);
 #endif
-        if (mode == M_LEARNED && d == D_SKIP) {
-            // still waiting: a continuation is this lane's (claimed for the
-            // next sweep already), an entry joins the next sweep once
-            if (check_ready == R_NOW) push[npush++] = i;
-            else learned_push(P, i, S.k + 1, push, npush);
+        // learned mode, still waiting: a continuation this lane claimed for
+        // the next sweep goes there; an entry is dropped, and the last of its
+        // arguments to become a normal form queues it (queueing it here would
+        // take the claim that argument needs to continue with it)
+        if (mode == M_LEARNED && d == D_SKIP && check_ready == R_NOW) push[npush++] = i;
+        if (own && (d >= 0 || d == D_MARK)) {
+            const int32_t want = d == D_MARK ? (int32_t)(S.k + 1) : -(int32_t)(S.k + 1);
+            if (atomicCAS(&P.nfs[i], s_seen, want) != s_seen) d = D_NONE;  // another lane has it
         }
     }
 #ifdef TRS_JIT
+    // learned mode with eager continuation allocates every new node: a slot
+    // consumed in the middle of a sweep may still be another lane's frontier
+    // entry, so it is not reused for a new node in the same sweep
+    if (own && d >= 0 && ((d >> 16) & 1)) d = (d & 0xffff) | (((T.rule(d & 0xffff)[0] >> 8) & 0xff) << 17);
     int m = (d >= 0) ? spec_new_count(d) : 0;
 #else
     int m = (d >= 0) ? ((T.rule(d)[0] >> 8) & 0xff) : 0;

@@ -385,12 +385,12 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
             ops.push_back(opnd(r.build[a]));
             o << "        arg_at(P, " << a << ", i) = " << ops.back() << ";\n";
         }
-        o << "        if (mode == M_LEARNED) {\n";
+        o << "        if (mode == M_LEARNED) {\n"
+             "            st_release_s32(&P.nfs[i], -(int32_t)(k + 1));\n";
         if (r.root_pend == 0) {
-            o << "            const int before = npush;\n            learned_push(P, i, k + 1, push, npush);\n"
-                 "            last.h = 0;\n            if (npush != before) {\n";
-            emit_carry("                ", r.rootval, ops);
-            o << "            }\n";
+            // the redex is this lane's: queued (or continued) without a claim
+            o << "            pend_at(P, i) = (int32_t)(k + 1);\n            push[npush++] = i;\n";
+            emit_carry("            ", r.rootval, ops);
         }
         o << "        } else {\n            pend_at(P, i) = " << r.root_pend << ";\n";
         if (r.root_pend == 0) {
