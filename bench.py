@@ -93,6 +93,16 @@ def arith_sweeps(meta):
     return out
 
 
+_TMSORT = {}
+
+
+def tmsort_input():
+    """Tree merge sort 23 5 (about 306M symbols), generated once per process."""
+    if not _TMSORT:
+        _TMSORT["v"] = ti.msort_uniform_batch(depth=23, length=5)
+    return _TMSORT["v"]
+
+
 def build_workload(name, seed=0):
     """(trs, flat, offsets, pool capacity, expected rewrites or None, description,
     autotune workload key, terms for the oracle sample)."""
@@ -116,7 +126,7 @@ def build_workload(name, seed=0):
         return (ti.MSORT, f, o, 1 << 24, None,
                 "merge sort of 256 lists (64..1024 numerals 0..31), single term, pool 2^24", "msort")
     if name == "tmsort23":
-        term, _ = ti.msort_uniform_batch(depth=23, length=5)
+        term, _ = tmsort_input()
         f, o = ti.concat_terms([term])
         return (ti.MSORT, f, o, 1 << 30, None,
                 "tree merge sort 23 5: 2^23 lists of 5 numerals 0..9 in one Node tree, pool 2^30", "msort")
@@ -566,23 +576,24 @@ def oracle_sample(name, target_s, threads=None):
     from oracle import Oracle, normalize_threads
     threads = threads or os.cpu_count() or 1
     if name == "tmsort23":
-        # the tree's rewrites all happen inside its leaves: Leaf(Sort(list))
-        # of each list normalised as a term of its own, on a seeded sample
-        _, vals = ti.msort_uniform_batch(depth=23, length=5)
+        # the tree's rewrites all happen inside its leaves (Node and Leaf have
+        # no rules): sub-trees of 4,096 consecutive lists, one term per host
+        # thread at a time, a seeded sample of them
+        _, vals = tmsort_input()
         rng = np.random.default_rng(1)
-        pick = rng.choice(len(vals), 1 << 16, replace=False)
-        terms = [ti.msort_tree_uniform(vals[i][None, :]) for i in pick]
+        order = rng.permutation(len(vals) // 4096)
         done, rew, t0 = 0, 0, time.perf_counter()
-        while done < len(terms):
-            res = normalize_threads(ti.MSORT, terms[done:done + 4096], threads)
+        while done < len(order):
+            part = [ti.msort_tree_uniform(vals[b * 4096:(b + 1) * 4096]) for b in order[done:done + threads]]
+            res = normalize_threads(ti.MSORT, part, threads)
             rew += sum(x.rewrites for x in res)
             done += len(res)
             if time.perf_counter() - t0 >= target_s:
                 break
         used = time.perf_counter() - t0
         return {"value": rew / used, "unit": UNIT, "cores": threads, "kind": "oracle",
-                "sample": f"{done} of the 2^23 lists (seeded sample), each Leaf(Sort(list)) a term, "
-                          f"{threads} host threads", "seconds": used}
+                "sample": f"{done * 4096} of the 2^23 lists (seeded sample of 4,096-list sub-trees, one "
+                          f"term per thread at a time), {threads} host threads", "seconds": used}
     t, flat, offs, _, _, _, _ = build_workload(name)
     nterms = len(offs) - 1
     terms = [flat[offs[i]:offs[i + 1]] for i in range(nterms)]

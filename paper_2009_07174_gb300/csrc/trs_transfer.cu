@@ -57,8 +57,14 @@ struct Ctl {
     int stopped;          // expansion has stopped
     int status;           // 0, TRS_ERR_STATE (corrupt store / dead root) or
                           // TRS_ERR_TOO_BIG (a depth-first stack would overflow)
-    int pad;
+    int overflow;         // the chunk pool ran out: emission walks the store again
+    unsigned long long chunk_next;  // chunks handed out
 };
+
+// The counting walk also keeps the symbols it visits, in chunks of kCh words
+// from a pool (word 0: the next chunk of the same item, or -1), so that the
+// emission copies them instead of walking the store a second time.
+constexpr int kCh = 64;
 
 __device__ __forceinline__ void fail(Ctl *c, int st) { atomicCAS(&c->status, 0, st); }
 
@@ -166,7 +172,7 @@ __global__ void k_expand_flip(Ctl *c, long long cap_items)
 // Size of every item: 1 for a symbol, the unfolded subtree for a reference
 // (depth first; the stack holds the pending right siblings).
 __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long long *sz, Ctl *c,
-                        long long limit_ns)
+                        long long limit_ns, int32_t *chunks, long long chunk_cap, int32_t *ihead)
 {
     const int32_t *it = items[c->cur];
     const long long n = c->n_items;
@@ -174,17 +180,37 @@ __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long 
         const int32_t x0 = it[e];
         if (x0 <= 0) {
             sz[e] = 1;
+            ihead[e] = -1;
             continue;
         }
         int32_t stk[kStack];
         int sp = 0;
         long long cntv = 0;
         int32_t x = x0;
+        int32_t head = -1, chk = -1;
+        int fill = kCh;
+        bool keep = true;
         const long long t0 = clock_ns();
         for (;;) {
             int32_t h = 0;
             if (!node_ok(P, n_top, x, h)) { fail(c, TRS_ERR_STATE); break; }
             cntv++;
+            if (keep) {
+                if (fill == kCh) {
+                    const unsigned long long nc = atomicAdd(&c->chunk_next, 1ull);
+                    if ((long long)nc >= chunk_cap) {
+                        keep = false;
+                        c->overflow = 1;
+                    } else {
+                        if (chk >= 0) chunks[(long long)chk * kCh] = (int32_t)nc;
+                        else head = (int32_t)nc;
+                        chk = (int32_t)nc;
+                        chunks[(long long)chk * kCh] = -1;
+                        fill = 1;
+                    }
+                }
+                if (keep) chunks[(long long)chk * kCh + fill++] = h;
+            }
             if ((cntv & 4095) == 0 && (clock_ns() - t0 > limit_ns || c->status)) {
                 fail(c, TRS_ERR_TIMEOUT);
                 break;
@@ -201,6 +227,38 @@ __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long 
             }
         }
         sz[e] = cntv;
+        ihead[e] = head;
+    }
+}
+
+// Emission from the kept chunks: the items whose output range meets [lo, hi).
+__global__ void k_copy(int32_t *const *items, const long long *off, const int32_t *ihead, const int32_t *chunks,
+                       int32_t *out, long long lo, long long hi, Ctl *c)
+{
+    if (c->status) return;
+    const int32_t *it = items[c->cur];
+    const long long n = c->n_items;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long pos = off[e];
+        const long long end = off[e + 1];
+        if (end <= lo || pos >= hi) continue;
+        const int32_t x0 = it[e];
+        if (x0 <= 0) {
+            out[pos - lo] = -x0;
+            continue;
+        }
+        long long ch = ihead[e];
+        int fill = 1;
+        while (pos < end && pos < hi && ch >= 0) {
+            if (fill == kCh) {
+                ch = chunks[ch * kCh];
+                fill = 1;
+                continue;
+            }
+            const int32_t sym = chunks[ch * kCh + fill++];
+            if (pos >= lo) out[pos - lo] = sym;
+            pos++;
+        }
     }
 }
 
@@ -625,10 +683,16 @@ int device_download(const DevPool &P, long long n_top, const int32_t *roots, int
         items_h[0] = (int32_t *)take((size_t)m * 4);
         items_h[1] = (int32_t *)take((size_t)m * 4);
         long long *vals = (long long *)take((size_t)(m + 1) * 8);
+        int32_t *ihead = (int32_t *)take((size_t)m * 4);
         if (off >= scratch_bytes) return TRS_ERR_TOO_BIG;
-        int32_t *stage = (int32_t *)(base + off);
-        const long long stage_cap = (long long)((scratch_bytes - off) / 4);
+        // the rest: a third for the output window, two thirds for the chunks
+        // the counting walk keeps
+        const long long rest = (long long)((scratch_bytes - off) / 4);
+        const long long stage_cap = rest / 3 / 64 * 64;
         if (stage_cap < 1024) return TRS_ERR_TOO_BIG;
+        int32_t *stage = (int32_t *)take((size_t)stage_cap * 4);
+        int32_t *chunks = (int32_t *)(base + off);
+        const long long chunk_cap = off < scratch_bytes ? (long long)((scratch_bytes - off) / 4) / dl::kCh : 0;
         const int grid = num_sms * 4;
 #define CUDA_STEP(call)                                    \
     do {                                                   \
@@ -652,7 +716,7 @@ int device_download(const DevPool &P, long long n_top, const int32_t *roots, int
             CUDA_STEP(cudaGetLastError());
         }
         // subtree sizes, output offsets, per-root offsets
-        dl::k_sizes<<<grid, dl::kThreads, 0, s>>>(P, n_top, items_ptr, vals, c, limit_ns);
+        dl::k_sizes<<<grid, dl::kThreads, 0, s>>>(P, n_top, items_ptr, vals, c, limit_ns, chunks, chunk_cap, ihead);
         CUDA_STEP(cudaGetLastError());
         CUDA_STEP(scan(vals, bsum, c, 2, 0, s));
         dl::k_root_offsets<<<grid, dl::kThreads, 0, s>>>(starts_ptr, vals, nr, roff, c);
@@ -668,7 +732,10 @@ int device_download(const DevPool &P, long long n_top, const int32_t *roots, int
         if (result == TRS_OK && out_total + tot <= cap) {
             for (long long lo = 0; lo < tot; lo += stage_cap) {
                 const long long hi = lo + stage_cap < tot ? lo + stage_cap : tot;
-                dl::k_emit<<<grid, dl::kThreads, 0, s>>>(P, n_top, items_ptr, vals, stage, lo, hi, c);
+                if (hc.overflow)
+                    dl::k_emit<<<grid, dl::kThreads, 0, s>>>(P, n_top, items_ptr, vals, stage, lo, hi, c);
+                else
+                    dl::k_copy<<<grid, dl::kThreads, 0, s>>>(items_ptr, vals, ihead, chunks, stage, lo, hi, c);
                 CUDA_STEP(cudaGetLastError());
                 CUDA_STEP(cudaMemcpyAsync(buf + out_total + lo, stage, (size_t)(hi - lo) * 4,
                                           cudaMemcpyDeviceToHost, s));

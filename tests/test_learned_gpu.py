@@ -432,3 +432,53 @@ def test_learned_against_exact_frontier_and_plain(env, fib_pred, record_property
     assert res["learned"]["visits"] >= acted
     assert res["learned"]["visits"] < 0.5 * res["plain"]["visits"]
     assert res["learned_eager"]["sweeps"] < res["learned"]["sweeps"]
+
+
+def _numeral_ok(t, pre, v):
+    return len(pre) == v + 1 and pre[-1] == t.id["0"] and (v == 0 or np.all(pre[:-1] == t.id["S"]))
+
+
+@pytest.mark.parametrize("which", ["config3", "config4"])
+def test_learned_batches_full_size(env, which):
+    """The batch configurations in learned mode at full size, with predictors
+    trained on the engine's traces of smaller batches of the same rules:
+    4,096 arithmetic trees (pool 2^29) and 10,000 fib(n) terms (pool 2^28).
+    The rewrite totals equal the closed forms (a + 1 per plus, a(b + 2) + 1
+    per times; T(n) for fib(n)) and every normal form is the numeral of the
+    term's value."""
+    torch, trs = env
+    from paper_2009_07174_gb300 import autotune_defaults, learn
+    if which == "config3":
+        t = ti.ARITH
+        flat, offs, meta = ti.arith_batch(seed=0, count=4096)
+        values, total = [], 0
+        for d, ops, vals in meta:
+            h = np.arange(1, 1 << d)
+            a, b = vals[2 * h], vals[2 * h + 1]
+            total += int(np.where(ops[h] == 1, a * (b + 2) + 1, a + 1).sum())
+            values.append(int(vals[1]))
+        tf, to, _ = ti.arith_batch(seed=7, count=64, dmin=10, dmax=11)
+        cap, key = 1 << 29, "arith-4096"
+    else:
+        t = ti.FIB
+        flat, offs, ns = ti.fib_batch(seed=0, count=10000)
+        F = [0, 1]
+        for _ in range(40):
+            F.append(F[-1] + F[-2])
+        T = [1, 1]
+        for k in range(2, 21):
+            T.append(T[k - 1] + T[k - 2] + F[k - 2] + 2)
+        values = [F[int(n)] for n in ns]
+        total = sum(T[int(n)] for n in ns)
+        tf, to = ti.concat_terms([ti.fib_term(n) for n in range(8, 21)])
+        cap, key = 1 << 28, "fib-batch-10000"
+    prog = trs.trs_compile(t).specialise()
+    pred = learn.train_for(prog, tf, to, 1 << 24, period=16)
+    pool = trs.Pool(prog, cap)
+    pool.trs_pool_attach_predictor(pred)
+    roots = pool.term_upload_batch(flat, offs)
+    st = pool.trs_normalize(**autotune_defaults("learned", key))
+    assert st["status"] == 0 and st["rewrites"] == total
+    got = pool.term_download_batch(roots, cap=sum(values) + len(values))
+    for g, v in zip(got, values):
+        assert _numeral_ok(t, g, v)
