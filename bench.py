@@ -129,7 +129,7 @@ def build_workload(name, seed=0):
         term, _ = tmsort_input()
         f, o = ti.concat_terms([term])
         return (ti.MSORT, f, o, 1 << 30, None,
-                "tree merge sort 23 5: 2^23 lists of 5 numerals 0..9 in one Node tree, pool 2^30", "msort")
+                "tree merge sort 23 5: 2^23 lists of 5 numerals 0..9 in one Node tree, pool 2^30", "tmsort23")
     if name == "ttree22":
         f, o = ti.concat_terms([ti.ttree_term(22)])
         return (ti.TTREE, f, o, 1 << 24, 28 * 2 ** 22 - 1,

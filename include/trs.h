@@ -403,8 +403,8 @@ int trs_pool_attach_predictor(trs_pool *pool, const trs_predictor *pred);
  * TRS_ERR_TOO_BIG before any GPU work; running out of slots while rewriting
  * returns TRS_ERR_POOL_FULL; a normal form longer than out_cap returns
  * TRS_ERR_BUFFER_SMALL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  Every call reuses the same array, which
+ * address (cudaGetSymbolAddress, with that device current).  Every call
+ * reuses the same array, which
  * keeps the previous call's contents (each call clears what it uses first):
  * calls whose GPU work overlaps -- on different streams or host threads --
  * race on the array, so serialise them. */

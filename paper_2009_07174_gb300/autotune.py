@@ -95,10 +95,13 @@ def tune(mode: str, make_pool, workload: str, reps: int = 2, space: dict | None 
          path: str = CACHE, verbose: bool = False) -> dict:
     """Time every candidate on pools from `make_pool()` (a fresh pool with the
     workload uploaded, returning (pool, expected_rewrites)); keep the fastest
-    whose rewrite count is right.  Returns {"opts", "ms", "tried"}."""
+    whose rewrite count is right.  Returns {"opts", "ms", "tried", "timed"}
+    (every candidate with a correct count and its best time); the choice
+    is cached without "timed"."""
     import torch
     best = None
     tried = 0
+    timed = []
     for o in candidates(mode, space):
         times = []
         ok = True
@@ -121,6 +124,7 @@ def tune(mode: str, make_pool, workload: str, reps: int = 2, space: dict | None 
         if not ok:
             continue
         ms = min(times)
+        timed.append({"opts": o, "ms": ms})
         if verbose:
             print(f"autotune {workload} {mode} {o} {ms:.3f} ms", flush=True)
         if best is None or ms < best["ms"]:
@@ -131,7 +135,7 @@ def tune(mode: str, make_pool, workload: str, reps: int = 2, space: dict | None 
     cache = load_cache(path)
     cache.setdefault(gpu_name(), {}).setdefault(workload, {})[mode] = best
     save_cache(cache, path)
-    return best
+    return dict(best, timed=timed)
 
 
 def workloads():

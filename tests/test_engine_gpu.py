@@ -239,3 +239,26 @@ def test_eager_continuation(trs, eager, solo):
 def test_block_sizes(trs, block):
     terms = [ti.fib_term(n) for n in range(5, 12)]
     check(trs, ti.FIB, terms, block_size=block)
+
+
+def test_autotune_picks_the_fastest_correct_candidate(trs, tmp_path):
+    """tune() on a small batch: every candidate is timed on a fresh pool and
+    checked against the expected rewrite count, and the option set it keeps
+    (and caches) is the fastest of them."""
+    from paper_2009_07174_gb300 import autotune
+    t = ti.FIB
+    prog = trs.trs_compile(t)
+    flat, offs, ns = ti.fib_batch(seed=3, count=300)
+    expect = Oracle(t)
+    total = sum(expect.normalize(flat[offs[i]:offs[i + 1]]).rewrites for i in range(len(ns)))
+
+    def make_pool():
+        pool = trs.Pool(prog, 1 << 22)
+        pool.term_upload_batch(flat, offs)
+        return pool, total
+    space = {"block_size": [128, 512], "solo_max": [0, 512], "eager": [0, 64], "driver": ["persistent"]}
+    cache = str(tmp_path / "tune.json")
+    best = autotune.tune("frontier", make_pool, "test-fib-300", reps=1, space=space, path=cache)
+    assert best["tried"] == 8 and len(best["timed"]) == 8
+    assert best["ms"] == min(c["ms"] for c in best["timed"])
+    assert autotune.choose("frontier", "test-fib-300", path=cache)["eager"] == best["opts"]["eager"]
