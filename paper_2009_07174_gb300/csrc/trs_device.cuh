@@ -97,6 +97,9 @@ __device__ __noinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, long long tim
             long long t0 = now_ns();
             int spins = 0;
             while (ld_relaxed_u32(&ctl->bar_gen) == gen) {
+                // back off once the wait is not short: the waiting blocks'
+                // loads all go to the one L2 slice that holds the barrier word
+                if (spins >= 64) __nanosleep(spins >= 512 ? 512 : 128);
                 if ((++spins & 63) == 0) {
                     if (ld_relaxed_s32(&ctl->status) != 0) { ok = 0; break; }
                     if (now_ns() - t0 > timeout_ns) { set_status(ctl, TRS_ERR_TIMEOUT); ok = 0; break; }
@@ -207,12 +210,14 @@ __device__ __forceinline__ void store_nf(const DevPool &P, int mode, int32_t i, 
     else P.nfs[i] = (int32_t)(k + 1);
 }
 
-// Content of a node this lane has just written (head and first arguments),
-// handed to the next step of an eager chain so that it need not be read back.
+// Content of a node this lane has just written (head, first arguments and
+// parent word), handed to the next step of an eager chain so that it need not
+// be read back.
 constexpr int kCarryArgs = 4;
 struct Carry {
     int32_t h;                  // 0: nothing carried
     int32_t c[kCarryArgs];
+    int32_t p;                  // parent word (valid when h != 0)
 };
 
 // Prefetch a node record into L1 (a hint: no register, no wait).  Used for
@@ -619,6 +624,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         hs_at(P, x) = sym;
         Carry cx;
         cx.h = na <= kCarryArgs ? sym : 0;
+        cx.p = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
         for (int a = 0; a < na; a++) {
             int32_t op = build[pos++];
             const int32_t v = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
@@ -627,7 +633,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         }
         rc_at(P, x) = 1;
         P.nfs[x] = stamp_new;
-        par_at(P, x) = parent < 0 ? par_word(T, i, R[1]) : par_word(T, nw[parent], build_sym(build, root_nargs, parent));
+        par_at(P, x) = cx.p;
         if (mode == M_LEARNED) {
             // a new node that waits for new arguments is queued (and
             // claimed) by the last of them to become a normal form
@@ -686,6 +692,7 @@ __device__ __forceinline__ void apply(const DevPool &P, const Tab &T, int mode, 
         hs_at(P, i) = R[1];
         Carry ci;
         ci.h = root_nargs <= kCarryArgs ? R[1] : 0;
+        ci.p = pv;  // a rewrite in place keeps the parent
         for (int a = 0; a < root_nargs; a++) {
             int32_t op = build[a];
             const int32_t v = (op >> 16) ? nw[op & 0xffff] : reg[op & 0xffff];
@@ -779,7 +786,7 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
     if (keep) learned_push(P, i, S.k + 1, push, npush);  // learned: not yet eligible, keep it
     // the parent word is loaded together with the node (it is needed when the
     // node turns out to be a normal form), not after the decision
-    const int32_t pv = (mode != M_PLAIN && cand) ? par_at(P, i) : 0;
+    const int32_t pv = (mode != M_PLAIN && cand) ? (carry.h != 0 ? carry.p : par_at(P, i)) : 0;
     // learned mode with eager continuation: a frontier entry and a lane's
     // claimed continuation can be the same node, so a lane owns a step only
     // once it has swapped the node's stamp from the value it read before
@@ -896,6 +903,7 @@ __device__ __forceinline__ int32_t process_warp(const DevPool &P, const Tab &T, 
                 cont = p;
                 carry.h = ph;
                 carry.c[0] = child;
+                carry.p = rec_par(rec_ma(P)) < 4 ? quad_word(q, rec_par(rec_ma(P))) : par_at(P, p);
                 break;
             }
             P.nfs[p] = (int32_t)(S.k + 1);

@@ -285,13 +285,15 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
     };
     // the content of a node that becomes the eager continuation (its
     // arguments' records are prefetched for the next step)
-    auto emit_carry = [&](const std::string &ind, int sym, const std::vector<std::string> &ops) {
+    auto emit_carry = [&](const std::string &ind, int sym, const std::vector<std::string> &ops,
+                          const std::string &parw) {
         const int na = (int)ops.size();
         for (int a : inspected_args(P, sym))
             if (a < na) o << ind << "prefetch_rec(P, " << ops[a] << ");\n";
         if (na <= 4) {
             o << ind << "last.h = " << sym << ";\n";
             for (int a = 0; a < na; a++) o << ind << "last.c[" << a << "] = " << ops[a] << ";\n";
+            o << ind << "last.p = " << parw << ";\n";
         } else {
             o << ind << "last.h = 0;\n";
         }
@@ -338,12 +340,12 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
         o << "            if (mode == M_LEARNED) {\n";
         if (pj == 0) {
             o << "                push[npush++] = x;\n";
-            emit_carry("                ", sym, ops);
+            emit_carry("                ", sym, ops, "(" + parw + ")");
         }
         o << "            } else {\n";
         if (pj == 0) {
             o << "                if (mode == M_FRONTIER) {\n                    push[npush++] = x;\n";
-            emit_carry("                    ", sym, ops);
+            emit_carry("                    ", sym, ops, "(" + parw + ")");
             o << "                }\n";
         }
         o << "            }\n        }\n";
@@ -390,12 +392,12 @@ void gen_apply_body(std::ostringstream &o, const Program &P, const RuleView &r, 
         if (r.root_pend == 0) {
             // the redex is this lane's: queued (or continued) without a claim
             o << "            pend_at(P, i) = (int32_t)(k + 1);\n            push[npush++] = i;\n";
-            emit_carry("            ", r.rootval, ops);
+            emit_carry("            ", r.rootval, ops, "pv");
         }
         o << "        } else {\n            pend_at(P, i) = " << r.root_pend << ";\n";
         if (r.root_pend == 0) {
             o << "            if (mode == M_FRONTIER) {\n                push[npush++] = i;\n";
-            emit_carry("                ", r.rootval, ops);
+            emit_carry("                ", r.rootval, ops, "pv");
             o << "            }\n";
         }
         o << "        }\n";
