@@ -1186,6 +1186,9 @@ __device__ __forceinline__ void phase_gc_collect(const DevPool &P, const State &
         if (w < nwords) {
             v = P.dbm[w];
             if (v) P.dbm[w] = 0;
+            // bits of the last word above the high-water mark belong to no
+            // node of this run (a store reused without clearing its bitmap)
+            if (w * 32 + 32 > S.n) v &= S.n > w * 32 ? (1u << (S.n - w * 32)) - 1u : 0u;
         }
         const int cnt = __popc(v);
         int x = cnt;

@@ -101,14 +101,13 @@ __global__ void k_static_upload(DevPool P, const int32_t *term, long long len, i
             int32_t parent = stk_node[sp - 1];
             int32_t j = stk_next[sp - 1]++;
             arg_at(P, j, parent) = node;
-            par_at(P, node) = parent;
+            // the parent word: sign bit set when the parent's head is unary
+            par_at(P, node) = parent | ((ar[hs_at(P, parent)] & 0xff) == 1 ? (int32_t)0x80000000 : 0);
             if (stk_next[sp - 1] == (ar[hs_at(P, parent)] & 0xff)) sp--;
         }
         if ((ar[s] & 0xff) > 0) { stk_node[sp] = node; stk_next[sp] = 0; sp++; }
     }
     if (sp != 0) { c->status = TRS_ERR_BAD_TERM; return; }
-    // candidate bits a previous call left below the new high-water mark
-    for (long long w = 0; w <= len / 32; w++) P.dbm[w] = 0;
     c->sweep_id = 1;
     c->n_top = len + 1;
     c->fl_begin = c->fl_end = 0;
@@ -209,8 +208,14 @@ extern "C" int trs_normalize_static(const trs_program *prog, const int32_t *d_te
     lo.threshold = o.threshold;
     lo.timeout_ns = o.timeout_ns;
     lo.time_limit_ns = o.time_limit_ns;
-    // clear the control block, copy the rule table, build, normalise, serialise
+    // clear the control block, every stamp and the candidate bitmap (a
+    // previous call leaves stamps and bits above this term's slots, and the
+    // engine hands slots above the high-water mark back to the free ring as
+    // free, stamp 0, without writing them), copy the rule table, build,
+    // normalise, serialise
     e = cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.nfs, 0, (size_t)cap * sizeof(int32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.dbm, 0, (size_t)(cap + 31) / 32 * sizeof(uint32_t), stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync((void *)d.tab, p.table.data(), p.table.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, stream);

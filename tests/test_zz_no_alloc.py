@@ -121,3 +121,24 @@ def test_static_device_errors_then_clean_call(env, spec):
     assert trs.STATUS[code] == "TRS_ERR_BUFFER_SMALL" and n == -1
     code, n, out = static_call(torch, trs, prog, good, len(want))
     assert code == 0 and n == len(want) and np.array_equal(out[:n].cpu().numpy(), want)
+
+
+def test_static_calls_after_larger_ones(env):
+    """Calls after larger ones: an earlier call leaves stamps, counts and
+    collection-candidate bits in the slots above a later, smaller term's.
+    None of it may leak into the later run (a leftover candidate bit on a
+    slot with a leftover stamp would free that slot a second time): every
+    later result must equal the oracle's, in both modes and both engines."""
+    torch, trs = env
+    big, small = ti.fib_term(18), ti.fib_term(15)   # fib(15) runs a collection in both modes
+    want = Oracle(ti.FIB).normalize(small)
+    for spec in (False, True):
+        prog = trs.trs_compile(ti.FIB)
+        if spec:
+            prog.specialise()
+        for mode in ("plain", "frontier"):
+            for _ in range(10):
+                via_static(torch, trs, prog, big, mode)
+                got, st = via_static(torch, trs, prog, small, mode)
+                assert np.array_equal(got, want.term)
+                assert st["rewrites"] == want.rewrites and st["nf_marks"] == want.nf_marks
