@@ -1007,13 +1007,16 @@ __device__ __forceinline__ void phase_plain(const DevPool &P, const Tab &T, cons
 // entries (one atomic per warp), so chains of dependent rewrites advance many
 // steps per sweep.  Results and counts are those of the synchronous sweep;
 // only the number of sweeps changes.
-// `narrow` (a grid sweep whose frontier has no more entries than the grid has
-// warps): a warp takes one entry at a time, and only when all its lanes are
-// idle, so each chain runs on a warp of its own and the constructor climb
-// (`climb`) holds no other lane back.
+// `lane_cap`: a warp keeps at most that many lanes busy.  A grid sweep whose
+// frontier has fewer entries than the grid has lanes spreads them over all
+// warps (about entries / warps per warp) instead of packing 32 chains into
+// each of the first warps to claim, which would leave most SMs idle and make
+// the packed chains diverge.  With a cap of 1 (no more entries than warps)
+// each chain runs on a warp of its own, and the constructor climb (`climb`)
+// holds no other lane back.
 __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, const State &S, Acc *A, int mode,
                                long long warp0, long long nwarps, int eager = 0, bool climb = false,
-                               bool narrow = false)
+                               int lane_cap = 32)
 {
     Counters C{0, 0, 0, 0, 0};
     WarpAlloc W = warp_alloc_begin(P, S);
@@ -1071,7 +1074,17 @@ __device__ __forceinline__ void phase_frontier(const DevPool &P, const Tab &T, c
             }
             const bool idle = node < 0;
             const unsigned im0 = __ballot_sync(kFull, idle);
-            const unsigned im = narrow ? (im0 == kFull ? 1u : 0u) : im0;
+            unsigned im = drained ? 0u : im0;
+            if (lane_cap < 32 && im) {
+                // the lowest idle lanes, up to the cap on busy lanes
+                const int allow = lane_cap - (32 - __popc(im0));
+                unsigned r = 0, m = im0;
+                for (int t = 0; t < allow && m; t++) {
+                    r |= m & (0u - m);
+                    m &= m - 1;
+                }
+                im = r;
+            }
             bool fresh_entry = false;
             int32_t kept = -1;   // learned: an entry not yet eligible, queued again
             if (im && !drained) {

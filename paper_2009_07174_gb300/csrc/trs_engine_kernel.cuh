@@ -253,7 +253,11 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
                 for (;;) {
                     if (threadIdx.x == 0) memset(&s_acc, 0, sizeof(Acc));
                     __syncthreads();
-                    phase_frontier(P, T, S, &s_acc, o.mode, threadIdx.x >> 5, wpb, o.eager, true);
+                    // the episode's frontier spread over the block's warps
+                    long long per = (S.fsz + wpb - 1) / wpb;
+                    if (per > 32) per = 32;
+                    if (per < 1) per = 1;
+                    phase_frontier(P, T, S, &s_acc, o.mode, threadIdx.x >> 5, wpb, o.eager, true, (int)per);
                     __syncthreads();
                     const AccVals V = read_acc(&s_acc, true);
                     F = end_sweep(S, V, o, P.cap);
@@ -327,8 +331,11 @@ k_engine(DevPool P, LaunchOpts o_in, long long budget, unsigned long long cond)
             Acc *A = &ctl->acc[S.k % 3];
             if (o.mode == M_PLAIN) phase_plain(P, T, S, A, gw0, gnw);
             else {
-                const bool narrow = o.eager > 0 && S.fsz <= gnw;
-                phase_frontier(P, T, S, A, o.mode, gw0, gnw, o.eager, narrow, narrow);
+                // busy lanes per warp: the frontier spread over every warp
+                long long per = (S.fsz + gnw - 1) / gnw;
+                if (o.eager <= 0 || per > 32) per = 32;
+                if (per < 1) per = 1;
+                phase_frontier(P, T, S, A, o.mode, gw0, gnw, o.eager, per == 1, (int)per);
             }
             if (!grid_sync(ctl, nblocks, o.timeout_ns)) goto out;
             const AccVals V = read_acc(A, false);
