@@ -1340,6 +1340,9 @@ __device__ __forceinline__ void phase_seed(const DevPool &P, const Tab &T, const
             else if (rdy) pend_at(P, i) = (int32_t)S.k;
             if (rdy) ready[nready++] = (int32_t)i;
         }
+        // a chunk without ready nodes (every chunk of a confirmation scan
+        // that finds nothing) costs one barrier instead of a block scan
+        if (!__syncthreads_or(nready > 0)) continue;
         int total = 0;
         const int off = block_scan_count(nready, &total);
         if (total > 0) {
