@@ -235,13 +235,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# the sources the engine kernel is built or generated from (the upload and
+# download kernels, the static entry point and the host API are not part of it)
+ENGINE_SOURCES = ("trs_compile.cpp", "trs_device.cuh", "trs_engine.h", "trs_engine_kernel.cuh",
+                  "trs_kernels.cu", "trs_mlp.cuh", "trs_spec.cpp")
+
+
 def kernel_source_hash():
-    """SHA-256 over the engine's CUDA sources: identifies the kernel version an
-    ncu capture was taken on."""
+    """SHA-256 over the engine kernel's sources: identifies the kernel version
+    an ncu capture was taken on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2009_07174_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in ENGINE_SOURCES:
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())

@@ -171,6 +171,13 @@ __global__ void k_expand_flip(Ctl *c, long long cap_items)
 
 // Size of every item: 1 for a symbol, the unfolded subtree for a reference
 // (depth first; the stack holds the pending right siblings).
+// Read-ahead: a chain built by rewriting usually lies in consecutive slots
+// (the rewrites reuse the slots of the numeral they consume in order, or take
+// consecutive fresh slots), so whenever the walk has to load a record it
+// loads the first words of the kAhead records from that slot on together,
+// and a node whose slot is among them costs no load of its own.
+constexpr int kAhead = 8;
+
 __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long long *sz, Ctl *c,
                         long long limit_ns, int32_t *chunks, long long chunk_cap, int32_t *ihead)
 {
@@ -191,9 +198,24 @@ __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long 
         int fill = kCh;
         bool keep = true;
         const long long t0 = clock_ns();
+        long long base = -kAhead - 1;   // slots base .. base + kAhead - 1 are in ahead[]
+        int4 ahead[kAhead];
         for (;;) {
-            int32_t h = 0;
-            if (!node_ok(P, n_top, x, h)) { fail(c, TRS_ERR_STATE); break; }
+            if (x < 1 || (long long)x >= n_top) { fail(c, TRS_ERR_STATE); break; }
+            if ((long long)x < base || (long long)x >= base + kAhead) {
+                base = x;
+#pragma unroll
+                for (int j = 0; j < kAhead; j++) {
+                    const long long y = base + j < n_top ? base + j : base;
+                    ahead[j] = *reinterpret_cast<const int4 *>(P.rec + y * P.rs);
+                }
+            }
+            int4 q = ahead[0];
+#pragma unroll
+            for (int j = 1; j < kAhead; j++)
+                if ((long long)x - base == j) q = ahead[j];
+            const int32_t h = q.x;
+            if (h < 1 || h >= P.nsym) { fail(c, TRS_ERR_STATE); break; }
             cntv++;
             if (keep) {
                 if (fill == kCh) {
@@ -219,8 +241,8 @@ __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long 
             const int a = arity_of(P.tab, h);
             if (a > 0) {
                 if (sp + a - 1 > kStack) { fail(c, TRS_ERR_TOO_BIG); break; }
-                for (int j = a - 1; j >= 1; j--) stk[sp++] = r[rec_arg(j)];
-                x = r[rec_arg(0)];
+                for (int j = a - 1; j >= 1; j--) stk[sp++] = j == 1 ? q.z : j == 2 ? q.w : r[rec_arg(j)];
+                x = q.y;
             } else {
                 if (sp == 0) break;
                 x = stk[--sp];
