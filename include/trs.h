@@ -404,10 +404,11 @@ int trs_pool_attach_predictor(trs_pool *pool, const trs_predictor *pred);
  * returns TRS_ERR_POOL_FULL; a normal form longer than out_cap returns
  * TRS_ERR_BUFFER_SMALL.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current).  Every call
- * reuses the same array, which
- * keeps the previous call's contents (each call clears what it uses first):
- * calls whose GPU work overlaps -- on different streams or host threads --
- * race on the array, so serialise them. */
+ * reuses the same array: it first clears the control block, every stamp and
+ * the collection-candidate bitmap (a previous call's node records may stay;
+ * nothing reads a slot before this call writes it).  Calls whose GPU work
+ * overlaps -- on different streams or host threads -- race on the array, so
+ * serialise them. */
 int trs_normalize_static(const trs_program *prog, const int32_t *d_term, int64_t len,
                          int32_t *d_out, int64_t out_cap, int64_t *d_out_len,
                          const trs_opts *opts, trs_stats *stats, trs_stream stream);
