@@ -254,32 +254,52 @@ __global__ void k_sizes(DevPool P, long long n_top, int32_t *const *items, long 
 }
 
 // Emission from the kept chunks: the items whose output range meets [lo, hi).
+// One warp takes 32 items: their lanes write the placed symbols, then the
+// warp copies each subtree item's chunks in turn, one chunk per step (lane l
+// moves symbols l + 1 and l + 33 of the chunk, coalesced), so that a long item
+// costs one dependent load (the next-chunk word) per 63 symbols.
 __global__ void k_copy(int32_t *const *items, const long long *off, const int32_t *ihead, const int32_t *chunks,
                        int32_t *out, long long lo, long long hi, Ctl *c)
 {
     if (c->status) return;
+    const unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int32_t *it = items[c->cur];
     const long long n = c->n_items;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        long long pos = off[e];
-        const long long end = off[e + 1];
-        if (end <= lo || pos >= hi) continue;
-        const int32_t x0 = it[e];
-        if (x0 <= 0) {
-            out[pos - lo] = -x0;
-            continue;
-        }
-        long long ch = ihead[e];
-        int fill = 1;
-        while (pos < end && pos < hi && ch >= 0) {
-            if (fill == kCh) {
-                ch = chunks[ch * kCh];
-                fill = 1;
-                continue;
+    const long long warp0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long g = warp0 * 32; g < n; g += nwarps * 32) {
+        const long long el = g + lane;
+        bool ref = false;
+        if (el < n) {
+            const long long pos = off[el];
+            const long long end = off[el + 1];
+            if (end > lo && pos < hi) {
+                const int32_t x0 = it[el];
+                if (x0 <= 0) out[pos - lo] = -x0;
+                else ref = true;
             }
-            const int32_t sym = chunks[ch * kCh + fill++];
-            if (pos >= lo) out[pos - lo] = sym;
-            pos++;
+        }
+        unsigned todo = __ballot_sync(kAll, ref);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const long long e = g + src;
+            const long long end = off[e + 1];
+            long long base = off[e];   // output position of the current chunk's first symbol
+            long long ch = ihead[e];
+            while (ch >= 0 && base < end && base < hi) {
+                if (base + (kCh - 1) > lo) {
+#pragma unroll
+                    for (int pass = 0; pass < 2; pass++) {
+                        const int k = 1 + lane + 32 * pass;
+                        const long long p = base + (k - 1);
+                        if (k < kCh && p < end && p >= lo && p < hi) out[p - lo] = chunks[ch * kCh + k];
+                    }
+                }
+                ch = chunks[ch * kCh];
+                base += kCh - 1;
+            }
         }
     }
 }
