@@ -827,6 +827,12 @@ int device_upload(const DevPool &P, const int32_t *flat, const int64_t *offsets,
     int32_t *st = (int32_t *)take((size_t)levels * nch * 4);
     long long *bsum = (long long *)take((size_t)(up::kScanBlocks + 1) * 8);
     const int grid = num_sms * 4;
+    // one thread per symbol for the passes whose threads wait on dependent
+    // loads of their own (the resolution of parents outside the chunk, the
+    // record writes): with a few threads per symbol range a warp waits for
+    // its slowest lane on every round, with one per symbol it retires early
+    const long long full = (total + up::kThreads - 1) / up::kThreads;
+    const int grid_full = (int)(full < 0x7fffffffLL ? (full > grid ? full : grid) : 0x7fffffffLL);
 #define UP_STEP(call)                                          \
     do {                                                       \
         cudaError_t e_ = (call);                               \
@@ -841,14 +847,14 @@ int device_upload(const DevPool &P, const int32_t *flat, const int64_t *offsets,
     up::k_local<<<grid, 128, 0, s>>>(d_e, total, d_par, st);
     UP_STEP(cudaGetLastError());
     for (int k = 1; k < levels; k++) up::k_table<<<grid, up::kThreads, 0, s>>>(st, nch, k);
-    up::k_resolve<<<grid, up::kThreads, 0, s>>>(d_e, total, d_par, st, nch, levels, c);
+    up::k_resolve<<<grid_full, up::kThreads, 0, s>>>(d_e, total, d_par, st, nch, levels, c);
     up::k_check<<<grid, up::kThreads, 0, s>>>(d_e, d_par, d_offs, nterms, bsum, up::kScanBlocks, c);
     UP_STEP(cudaGetLastError());
     up::Ctl hc;
     UP_STEP(cudaMemcpyAsync(&hc, c, sizeof(hc), cudaMemcpyDeviceToHost, s));
     UP_STEP(cudaStreamSynchronize(s));
     if (hc.status != 0) return TRS_ERR_BAD_TERM;
-    up::k_records<<<grid, up::kThreads, 0, s>>>(P, d_flat, d_e, d_par, total, base, stamp);
+    up::k_records<<<grid_full, up::kThreads, 0, s>>>(P, d_flat, d_e, d_par, total, base, stamp);
     UP_STEP(cudaGetLastError());
 #undef UP_STEP
     return TRS_OK;
