@@ -844,7 +844,8 @@ int device_upload(const DevPool &P, const int32_t *flat, const int64_t *offsets,
     up::k_sums<<<up::kScanBlocks, up::kThreads, 0, s>>>(d_flat, total, P.tab, P.nsym, bsum, c);
     up::k_top<<<1, 1024, 0, s>>>(bsum, up::kScanBlocks);
     up::k_open<<<up::kScanBlocks, up::kThreads, 0, s>>>(d_flat, total, nterms, P.tab, P.nsym, bsum, d_e, c);
-    up::k_local<<<grid, 128, 0, s>>>(d_e, total, d_par, st);
+    const long long lblocks = (nch + 127) / 128;   // one thread per chunk
+    up::k_local<<<(int)(lblocks > grid ? lblocks : grid), 128, 0, s>>>(d_e, total, d_par, st);
     UP_STEP(cudaGetLastError());
     for (int k = 1; k < levels; k++) up::k_table<<<grid, up::kThreads, 0, s>>>(st, nch, k);
     up::k_resolve<<<grid_full, up::kThreads, 0, s>>>(d_e, total, d_par, st, nch, levels, c);
