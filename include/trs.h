@@ -402,8 +402,9 @@ int trs_pool_attach_predictor(trs_pool *pool, const trs_predictor *pred);
  * rejected with
  * TRS_ERR_TOO_BIG before any GPU work; running out of slots while rewriting
  * returns TRS_ERR_POOL_FULL; a normal form longer than out_cap returns
- * TRS_ERR_BUFFER_SMALL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current).  Every call
+ * TRS_ERR_BUFFER_SMALL.  The first call on a device does a one-time set-up:
+ * it looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  Every call
  * reuses the same array: it first clears the control block, every stamp and
  * the collection-candidate bitmap (a previous call's node records may stay;
  * nothing reads a slot before this call writes it).  Calls whose GPU work
