@@ -27,7 +27,7 @@ DEFAULTS = {
 
 SPACE = {
     "plain": {"block_size": [128, 256, 512], "driver": ["persistent", "graph"]},
-    "frontier": {"block_size": [128, 256, 512], "solo_max": [0, 512], "eager": [0, 16, 64, 256, 1024],
+    "frontier": {"block_size": [128, 256, 512], "solo_max": [0, 64, 512], "eager": [0, 64, 256, 1024, 4096],
                  "driver": ["persistent", "graph"]},
     "learned": {"block_size": [256, 512], "solo_max": [0, 512], "refresh": [16, 64],
                 "threshold": [0.2, 0.5, 0.8], "eager": [0, 64, 256, 1024]},
