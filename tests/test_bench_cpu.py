@@ -83,3 +83,24 @@ def test_reference_arm_line(tmp_path):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_kernel_source_hash_covers_the_engine_sources_only(bench, tmp_path, monkeypatch):
+    """The hash that ties a counter capture to a kernel version reads exactly
+    the sources the engine kernel is built or generated from: changing one of
+    them changes it, changing the transfer kernels (upload, download) does not."""
+    import shutil
+    csrc = os.path.join(ROOT, "paper_2009_07174_gb300", "csrc")
+    for f in bench.ENGINE_SOURCES:
+        assert os.path.exists(os.path.join(csrc, f)), f
+    root = tmp_path / "repo"
+    shutil.copytree(csrc, root / "paper_2009_07174_gb300" / "csrc")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h0 = bench.kernel_source_hash()
+    assert h0 == bench.kernel_source_hash()
+    with open(root / "paper_2009_07174_gb300" / "csrc" / "trs_transfer.cu", "a") as fh:
+        fh.write("\n// not part of the engine kernel\n")
+    assert bench.kernel_source_hash() == h0
+    with open(root / "paper_2009_07174_gb300" / "csrc" / "trs_device.cuh", "a") as fh:
+        fh.write("\n// part of the engine kernel\n")
+    assert bench.kernel_source_hash() != h0
